@@ -1,0 +1,232 @@
+"""Pins of the oracle's boundary-layer preconditioner (Sec. 3.1, 3.2) and its
+FGMRES (Sec. 3.3)."""
+import numpy as np
+import pytest
+from scipy.linalg import solve_triangular
+
+import oracle
+from paper_2108_13468_gb300 import inputs
+from tests.conftest import read_table
+from tests.test_oracle_discretization import mms_problem
+
+
+def _problem(N, eps, seed=0):
+    x, _ = oracle.mesh(N, eps)
+    y = x.copy()
+    p = inputs.problem_fourier_quadratic(x, y, N, eps, seed=seed)
+    return x, y, p, oracle.assemble(N, eps, x, y, p.c1, p.c2, p.r)
+
+
+def regions(N):
+    """Block label of each interior unknown (x-fastest): C, X, Y, I (Sec. 3.1)."""
+    m = N // 2
+    lab = np.empty((N - 1, N - 1), "<U1")
+    for j in range(1, N):
+        for i in range(1, N):
+            lab[j - 1, i - 1] = ("C" if j <= m else "X") if i <= m else ("Y" if j <= m else "I")
+    return lab.ravel()
+
+
+def mhat_dense(N, A):
+    """The idealised M-hat of Sec. 3.1 built from the dense A by the
+    definition eq. (2D blocks): block order C < X < Y < I, lower blocks
+    zeroed, off-diagonal upper blocks exact, A_CC exact, and inside the
+    diagonal blocks: M_II = upper-triangular part of A_II (E, N kept);
+    M_YY drops W (keeps S, N, E); M_XX drops S (keeps W, E, N)."""
+    D = oracle.dense(N, A)
+    lab = regions(N)
+    order = {"C": 0, "X": 1, "Y": 2, "I": 3}
+    n = D.shape[0]
+    M = np.zeros_like(D)
+    M1 = N - 1
+    for p in range(n):
+        for q in np.nonzero(D[p])[0]:
+            bp, bq = order[lab[p]], order[lab[q]]
+            if bq < bp:
+                continue                         # lower block: zero
+            if bq > bp or lab[p] == "C" or p == q:
+                M[p, q] = D[p, q]                # upper block, A_CC, diagonal
+                continue
+            d = q - p                            # same block, off-diagonal
+            kind = {1: "E", -1: "W", M1: "N", -M1: "S"}[d]
+            keep = {"I": "EN", "Y": "SNE", "X": "WEN"}[lab[p]]
+            if kind in keep:
+                M[p, q] = D[p, q]
+    return M
+
+
+@pytest.mark.parametrize("N", [8, 12, 16])
+def test_precond_definition_dense(N):
+    """Oracle sweeps (M_II Gauss-Seidel, ordered Thomas line solves, block
+    back substitution) equal a dense solve with M-hat as eq. (2D blocks)
+    defines it; the transpose equals a dense solve with M-hat^T."""
+    for eps in (1e-2, 1e-5, 1e-8):
+        x, y, p, A = _problem(N, eps)
+        P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r, corner_exact=True)
+        Mh = mhat_dense(N, A)
+        v = np.random.default_rng(1).standard_normal((N - 1) ** 2)
+        z, _ = P.apply(v)
+        np.testing.assert_allclose(z, np.linalg.solve(Mh, v), rtol=1e-9, atol=1e-12 * np.abs(z).max())
+        zt, _ = P.apply(v, transpose=True)
+        np.testing.assert_allclose(zt, np.linalg.solve(Mh.T, v), rtol=1e-9, atol=1e-12 * np.abs(zt).max())
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-5, 1e-8])
+def test_regular_splitting(eps):
+    """Sec. 3.1: A = M-hat - N-hat is a regular splitting, so
+    rho(I - M-hat^{-1} A) < 1; every dropped entry is a diffusion coupling
+    eps/(hb h) or eps/(kb k) at a node whose spacing in that direction is the
+    coarse (interior) one."""
+    N = 16
+    x, y, p, A = _problem(N, eps)
+    D = oracle.dense(N, A)
+    Mh = mhat_dense(N, A)
+    Nh = Mh - D
+    assert (Nh >= 0).all()
+    assert (np.linalg.inv(Mh) >= -1e-12 * np.abs(np.linalg.inv(Mh)).max()).all()
+    rho = np.abs(np.linalg.eigvals(np.eye(D.shape[0]) - np.linalg.solve(Mh, D))).max()
+    assert rho < 1
+    H = x[-1] - x[-2]
+    p_, q_ = np.nonzero(Nh)
+    for pp, qq in zip(p_, q_):
+        assert np.isclose(Nh[pp, qq], eps / H ** 2, rtol=1e-9)   # hb = h = H there
+    # and the bound of Sec. 3.1 in its ingredient form: ||N-hat||_inf <= 2 eps / H^2
+    assert np.abs(Nh).sum(axis=1).max() <= 2 * eps / H ** 2 * (1 + 1e-9)
+
+
+def test_gs_is_textbook_backward_gauss_seidel():
+    """The downstream sweep (top-right to bottom-left) equals
+    e_new = (D + U)^{-1} (b - L e_old) with the lexicographic splitting of
+    the corner operator; the transposed sweep is forward Gauss-Seidel on A^T."""
+    N, eps = 32, 1e-5
+    x, y, p, A = _problem(N, eps)
+    P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r)
+    for l in range(P.nlev):
+        m = P.level_size(l)
+        _, _, L = P.level(l)
+        Ad = oracle.dense(m + 1, L)
+        rng = np.random.default_rng(l)
+        b, e = rng.standard_normal((2, m * m))
+        want = solve_triangular(np.triu(Ad), b - np.tril(Ad, -1) @ e, lower=False)
+        np.testing.assert_allclose(P.gs(l, b, e), want, rtol=1e-10, atol=1e-14 * np.abs(want).max())
+        At = Ad.T
+        want = solve_triangular(np.tril(At), b - np.triu(At, 1) @ e, lower=True)
+        np.testing.assert_allclose(P.gs(l, b, e, transpose=True), want, rtol=1e-10,
+                                   atol=1e-14 * np.abs(want).max())
+
+
+def test_level_zero_is_A_CC_and_coarse_geometry():
+    """Level 0 of the corner hierarchy is exactly the corner block A_CC; each
+    coarser level keeps every other node, the transition node, and the outer
+    node at the fine spacing H (the reading the 5-cycle count below pins)."""
+    N, eps = 64, 1e-6
+    x, y, p, A = _problem(N, eps)
+    P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r)
+    m = N // 2
+    D = oracle.dense(N, A)
+    idx = np.array([(j - 1) * (N - 1) + (i - 1) for j in range(1, m + 1) for i in range(1, m + 1)])
+    xs, ys, L0 = P.level(0)
+    np.testing.assert_array_equal(oracle.dense(m + 1, L0), D[np.ix_(idx, idx)])
+    assert [P.level_size(l) for l in range(P.nlev)] == [32, 16, 8, 4, 2]
+    for l in range(P.nlev):
+        xs, ys, _ = P.level(l)
+        ml = P.level_size(l)
+        assert xs[ml] == x[m] and xs[ml + 1] == x[m + 1]
+        assert np.allclose(np.diff(xs[: ml + 1]), x[m] / ml)
+
+
+def test_interpolation_and_fe_restriction():
+    """P reproduces functions bilinear in (x, y) that vanish on x=0, y=0;
+    restriction is the FE-scaled adjoint: <R r, e_c>_{D_c} = <r, P e_c>_{D_f}."""
+    N, eps = 64, 1e-6
+    x, y, p, A = _problem(N, eps)
+    P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r)
+    for l in range(P.nlev - 1):
+        xf, yf, Lf = P.level(l)
+        xc, yc, Lc = P.level(l + 1)
+        mf, mc = P.level_size(l), P.level_size(l + 1)
+        XC, YC = np.meshgrid(xc[1:mc + 1], yc[1:mc + 1])
+        XF, YF = np.meshgrid(xf[1:mf + 1], yf[1:mf + 1])
+        np.testing.assert_allclose(P.prolong(l, (XC * YC).ravel()), (XF * YF).ravel(), rtol=1e-12)
+        rng = np.random.default_rng(l)
+        r, ec = rng.standard_normal(mf * mf), rng.standard_normal(mc * mc)
+        lhs = (Lc["D"] * P.restrict(l, r)) @ ec
+        rhs = (Lf["D"] * r) @ P.prolong(l, ec)
+        assert np.isclose(lhs, rhs, rtol=1e-12)
+
+
+def test_corner_cycle_count_matches_paper():
+    """Sec. 3.2 (two exponential layers): the stationary iteration reaches the
+    10^3 reduction 'in 5 iterations for the results reported'."""
+    for N in (128, 256):
+        for eps in (1e-4, 1e-7):
+            x, y, c1, c2, r, f, ue = mms_problem("exp", N, eps)
+            P = oracle.Prec(N, eps, x, y, c1, c2, r)
+            A = oracle.assemble(N, eps, x, y, c1, c2, r)
+            _, st, it, rr, mc = oracle.fgmres(N, A, f, P, tol=10 * np.log(N) / N, tol_abs=True, scaled=False)
+            assert mc == 5, (N, eps, mc)
+
+
+def test_fgmres_iterations_match_paper_table():
+    """Sec. 3.3, tab:exponential_times_iters (iteration counts), paper stopping
+    rule ||R||_2 <= 10 N^-1 ln N on the eq. (exponential_MMS) problem."""
+    header, rows = read_table("table_exponential_iterations.txt")
+    for eps_s, vals in rows.items():
+        for N, ref in zip((128, 256), vals[:2]):
+            eps = float(eps_s)
+            x, y, c1, c2, r, f, ue = mms_problem("exp", N, eps)
+            P = oracle.Prec(N, eps, x, y, c1, c2, r)
+            A = oracle.assemble(N, eps, x, y, c1, c2, r)
+            u, st, it, rr, mc = oracle.fgmres(N, A, f, P, tol=10 * np.log(N) / N, tol_abs=True, scaled=False,
+                                              restart=100)
+            assert st == 0 and it == int(ref), (eps, N, it, ref)
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-8])
+def test_fgmres_reaches_direct_solution(eps):
+    N = 64
+    x, y, p, A = _problem(N, eps)
+    P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r)
+    u, st, it, rr, mc = oracle.fgmres(N, A, p.f, P, tol=1e-12)
+    ue = oracle.band_solve(N, A, p.f)
+    assert st == 0 and rr <= 1e-12
+    assert np.abs(u - ue).max() <= 1e-9 * np.abs(ue).max()
+    ut, st, it, rr, mc = oracle.fgmres(N, A, p.f, P, tol=1e-12, transpose=True)
+    assert st == 0
+    np.testing.assert_allclose(ut, oracle.band_solve(N, A, p.f, transpose=True), rtol=0,
+                               atol=1e-9 * np.abs(ut).max())
+
+
+def test_fixed_cycle_preconditioner_transpose_is_adjoint():
+    """With a fixed number of corner cycles M^{-1} is linear and the
+    transposed application is its exact adjoint: <M^{-1}a, b> = <a, M^{-T}b>."""
+    N, eps = 32, 1e-5
+    x, y, p, A = _problem(N, eps)
+    P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r, fixed_cycles=3)
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal((2, (N - 1) ** 2))
+    za, _ = P.apply(a)
+    zb, _ = P.apply(b, transpose=True)
+    assert np.isclose(za @ b, a @ zb, rtol=1e-10)
+    m = N // 2
+    ca, cb = rng.standard_normal((2, m * m))
+    ea, _ = P.corner_solve(ca)
+    eb, _ = P.corner_solve(cb, transpose=True)
+    assert np.isclose(ea @ cb, ca @ eb, rtol=1e-10)
+
+
+def test_two_grid_uniform_mesh_contracts():
+    """With eps = 1 the mesh is uniform and the corner problem is a mildly
+    convective Poisson problem: the V(1,1) cycle contracts by well under 0.25."""
+    N, eps = 64, 1.0
+    x, y, p, A = _problem(N, eps)
+    P = oracle.Prec(N, eps, x, y, p.c1, p.c2, p.r)
+    m = N // 2
+    _, _, L0 = P.level(0)
+    Ad = oracle.dense(m + 1, L0)
+    b = np.random.default_rng(0).standard_normal(m * m)
+    e = np.zeros(m * m)
+    r0 = np.linalg.norm(b)
+    for _ in range(4):
+        e = P.vcycle(0, b, e)
+    assert np.linalg.norm(b - Ad @ e) / r0 < 0.25 ** 4
