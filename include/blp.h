@@ -1,0 +1,149 @@
+/*
+ * blp.h -- C ABI of the GB300 boundary-layer-preconditioned solver.
+ *
+ * Solves the upwind finite-difference discretisation of
+ *     -eps * Lap(u) - c . grad(u) + r u = f   on (0,1)^2,  u = 0 on the boundary
+ * (MacLachlan, Madden & Nhan, arXiv 2108.13468, eq. (2D) and the 5-point
+ * stencil of Sec. 3) on a tensor-product Shishkin mesh (Sec. 3, eq. (tau
+ * exponential)), by restarted flexible GMRES (Sec. 3.3) right-preconditioned
+ * with the block-upper-triangular boundary-layer preconditioner of Sec. 3.1,
+ * eq. (2D blocks), whose corner block is approximated by the multigrid
+ * iteration of Sec. 3.2.
+ *
+ * Conventions shared by every call:
+ *  - N is the number of mesh intervals per axis (even, 8 <= N <= 16384).
+ *    Grid functions live on the (N-1)^2 interior nodes (x_i, y_j),
+ *    1 <= i, j <= N-1, stored x-fastest: index (j-1)*(N-1) + (i-1), double.
+ *  - Array arguments may be host or device (CUDA) pointers; the library
+ *    queries the pointer kind and stages host arrays through its own device
+ *    buffers.  The caller keeps ownership of every array it passes; the
+ *    library never frees or retains caller pointers after a call returns.
+ *  - All calls return an int status (BLP_OK = 0 on success, BLP_ERR_* on
+ *    failure); nothing is thrown across the ABI.  On error the output arrays
+ *    hold the best values computed so far (documented per call).
+ *  - Work is issued on the stream set with blp_set_stream (default: the
+ *    legacy default stream); calls return after the work has completed.
+ *  - A handle is not thread safe; use one handle per host thread.
+ */
+#ifndef BLP_H
+#define BLP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BLP_OK 0
+#define BLP_ERR_ARG 1      /* invalid argument (N odd or out of range, eps not in (0,1], null pointer, ...) */
+#define BLP_ERR_COEF 2     /* coefficients violate the assumptions of Sec. 3: c1 < beta_x, c2 < beta_y, r < 0, or non-finite */
+#define BLP_ERR_NOCONV 3   /* iteration limit reached before the tolerance */
+#define BLP_ERR_TIMEOUT 4  /* a bounded device-side wait gave up (the kernel recorded it and returned) */
+#define BLP_ERR_CUDA 5     /* a CUDA runtime call failed */
+#define BLP_ERR_MEM 6      /* device or host allocation failed */
+
+/* precision of the solve */
+#define BLP_FP64 0   /* everything in double precision */
+#define BLP_MIXED 1  /* FP32 preconditioner and inner FGMRES inside FP64 iterative refinement */
+
+/* stopping rules */
+#define BLP_STOP_SCALED 0   /* ||D^-1 (f - A u)||_2 <= tol ||D^-1 f||_2, D = diag(A) (default) */
+#define BLP_STOP_REL2 1     /* ||f - A u||_2 <= tol ||f||_2 (unscaled; FP64 floor may exceed tol for tiny eps) */
+#define BLP_STOP_ABS2 2     /* ||f - A u||_2 <= tol (tol = 10 ln(N)/N reproduces the paper's rule, Sec. 3.3) */
+
+typedef struct blp_handle blp_handle;
+
+/* Problem and solver parameters.  Call blp_params_default first. */
+typedef struct {
+    double eps;                /* perturbation parameter, 0 < eps <= 1 */
+    int N;                     /* intervals per axis */
+    double sigma;              /* transition-point factor: tau = min(1/2, sigma*eps*ln(N)/beta) (default 2) */
+    double beta_x, beta_y;     /* lower bounds of c1, c2 (default 1, 1) */
+    int restart;               /* FGMRES restart length m (default 30) */
+    int maxit;                 /* total FGMRES iteration limit (default 20000) */
+    int precision;             /* BLP_FP64 or BLP_MIXED */
+    int stop_mode;             /* BLP_STOP_* */
+    double corner_reduction;   /* corner multigrid residual reduction factor (default 1e3, Sec. 3.2) */
+    int corner_max_cycles;     /* cap on corner cycles per application (default 50) */
+    int corner_fixed_cycles;   /* >0: exactly this many corner cycles (M becomes a fixed linear map) */
+    double inner_tol;          /* BLP_MIXED: relative tolerance of each FP32 inner solve (default 1e-5) */
+    int inner_maxit;           /* BLP_MIXED: iteration cap of each inner solve (default 300) */
+    int check_coefficients;    /* nonzero: blp_setup validates c1, c2, r (default 1) */
+} blp_params;
+
+/* Statistics of the last solve. */
+typedef struct {
+    int status;             /* same as the return value */
+    int iters;              /* FGMRES iterations (inner iterations for BLP_MIXED) */
+    int restarts;           /* FGMRES restart cycles (outer refinement steps for BLP_MIXED) */
+    int corner_cycles_max;  /* largest corner multigrid cycle count in any preconditioner application */
+    double relres;          /* final relative residual in the stop_mode's norm (FP64, true residual) */
+    double relres_unscaled; /* ||f - A u||_2 / ||f||_2 (FP64) */
+    double t_solve_ms;      /* wall time of the solve call */
+    double t_setup_ms;      /* wall time of blp_setup for this handle */
+} blp_info;
+
+/* Fill *p with defaults: eps = 1e-4, N = 128, sigma = 2, beta = 1, restart
+ * 30, maxit 20000, FP64, scaled stopping, corner_reduction 1e3, 50 max
+ * cycles, no fixed cycles, inner_tol 1e-5, inner_maxit 300, checks on. */
+void blp_params_default(blp_params *p);
+
+/* S0. Shishkin mesh nodes (Sec. 2.2 eq. (tau 1D), Sec. 3 eq. (tau exponential)):
+ * tau = min(1/2, sigma*eps*ln(N)/beta), N/2 equal intervals on [0,tau] and
+ * on [tau,1]; x_i = (i/(N/2)) tau for i <= N/2, tau + ((i-N/2)/(N/2))(1-tau)
+ * above, x_N = 1.  x: host array of N+1 doubles (caller-owned).  Returns tau,
+ * or a negative value for invalid arguments. */
+double blp_mesh(int N, double eps, double sigma, double beta, double *x);
+
+/* Assemble the operator (Sec. 3 stencil) and build the preconditioner
+ * (Sec. 3.1 blocks, line factorisations, Sec. 3.2 corner hierarchy) on the
+ * current CUDA device.  c1, c2, r: (N-1)^2 values at the interior nodes of
+ * the mesh blp_mesh returns for (N, eps, sigma, beta_x) in x and beta_y in y.
+ * On success *out owns all device memory of the solver; release it with
+ * blp_destroy.  Errors: BLP_ERR_ARG, BLP_ERR_COEF (when check_coefficients),
+ * BLP_ERR_MEM, BLP_ERR_CUDA; *out is NULL then. */
+int blp_setup(const blp_params *p, const double *c1, const double *c2, const double *r, blp_handle **out);
+
+/* Issue all further work of this handle on `stream` (a cudaStream_t). */
+int blp_set_stream(blp_handle *h, void *stream);
+
+/* Solve A u = f (Sec. 3.3 FGMRES with the Sec. 3.1 preconditioner).
+ * f: right-hand side; u: initial guess on entry, solution on exit.
+ * tol: tolerance for the handle's stop_mode.  info may be NULL.
+ * BLP_ERR_NOCONV leaves the last iterate in u and its residual in info. */
+int blp_solve(blp_handle *h, const double *f, double *u, double tol, blp_info *info);
+
+/* Solve the adjoint system A^T lambda = g with the transposed preconditioner
+ * M^T (block lower triangular, applied C, X, Y, I).  Same conventions as
+ * blp_solve; lambda holds the initial guess on entry. */
+int blp_solve_adjoint(blp_handle *h, const double *g, double *lambda, double tol, blp_info *info);
+
+/* Adjoint gradient assembly for J(u(c1, c2, r, f)) with A u = f and
+ * A^T lambda = dJ/du:  dJ/df = lambda,  dJ/dr = -lambda u,
+ * dJ/dc1 = -lambda (u - u_E)/h_{i+1},  dJ/dc2 = -lambda (u - u_N)/k_{j+1}
+ * (u_E, u_N the east/north neighbours, 0 on the boundary).  Any of the
+ * three outputs may be NULL.  The mesh is held fixed. */
+int blp_grad(blp_handle *h, const double *u, const double *lambda, double *g_c1, double *g_c2, double *g_r);
+
+/* y = A u (transpose != 0: y = A^T u), unscaled operator, FP64. */
+int blp_apply_operator(blp_handle *h, const double *u, double *y, int transpose);
+
+/* One application of the preconditioner of the row-normalised system
+ * D^-1 A (D = diag(A)): z = (D^-1 M)^-1 v = M^-1 D v, or with transpose != 0
+ * z = (D^-1 M)^-T v.  precision: BLP_FP64 or BLP_MIXED (FP32 arithmetic).
+ * *cycles (may be NULL) receives the corner multigrid cycle count. */
+int blp_precond_apply(blp_handle *h, const double *v, double *z, int transpose, int precision, int *cycles);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void blp_destroy(blp_handle *h);
+
+/* Static description of a status code. */
+const char *blp_strerror(int status);
+
+/* Number of kernels this handle has launched since blp_setup (a counter the
+ * library keeps; used to report launch counts of timed regions). */
+long long blp_kernel_launches(const blp_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

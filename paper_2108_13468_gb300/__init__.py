@@ -1,0 +1,160 @@
+"""GB300-native boundary-layer-preconditioned solver for singularly perturbed
+convection-diffusion (MacLachlan, Madden & Nhan, arXiv 2108.13468).
+
+Python surface over the C ABI of ``include/blp.h`` (libblp.so):
+
+    x = mesh(N, eps)                       # Shishkin nodes (Sec. 3)
+    s = Solver(N, eps, c1, c2, r)          # blp_setup: assembly + preconditioner
+    u, info = s.solve(f, tol=1e-10)        # blp_solve: FGMRES + boundary-layer preconditioner
+    lam, info = s.solve_adjoint(g)         # blp_solve_adjoint
+    g1, g2, gr = s.grad(u, lam)            # blp_grad
+    u = solve(f, c1, c2, r, N=..., eps=...)  # differentiable (torch.autograd.Function)
+
+Arrays are float64 torch tensors (CUDA or CPU) or numpy arrays with
+(N-1)**2 entries, x-fastest over the interior nodes.  All arithmetic runs in
+libblp.so; this module only passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N_
+from ._native import (BLP_FP64, BLP_MIXED, BLP_STOP_ABS2, BLP_STOP_REL2, BLP_STOP_SCALED, BlpError, Info,
+                      Params)
+
+__all__ = ["mesh", "Solver", "Params", "Info", "BlpError", "BLP_FP64", "BLP_MIXED", "BLP_STOP_SCALED",
+           "BLP_STOP_REL2", "BLP_STOP_ABS2", "default_params", "solve"]
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    N_.load().blp_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0):
+    """Shishkin mesh nodes x[0..N] (blp_mesh) and the transition point tau."""
+    x = np.zeros(N + 1)
+    tau = N_.load().blp_mesh(N, eps, sigma, beta, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if tau < 0:
+        raise BlpError(N_.BLP_ERR_ARG, "blp_mesh")
+    return x, tau
+
+
+def _ptr(a, n, writable=False):
+    """(pointer, keepalive) for a float64 contiguous array of n values."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+                raise ValueError(f"expected a contiguous float64 tensor of {n} values")
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != n:
+        raise ValueError(f"expected a contiguous float64 array of {n} values")
+    if writable and not a.flags["WRITEABLE"]:
+        raise ValueError("output array is read-only")
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+class Solver:
+    """One assembled problem on the current CUDA device (blp_setup)."""
+
+    def __init__(self, N, eps, c1, c2, r, stream=None, **params):
+        self.lib = N_.load()
+        self.N = N
+        self.n = (N - 1) ** 2
+        self.params = default_params(N=N, eps=eps, **params)
+        h = ctypes.c_void_p()
+        self._h = None
+        args = [_ptr(a, self.n)[0] for a in (c1, c2, r)]
+        N_.check(self.lib.blp_setup(ctypes.byref(self.params), *args, ctypes.byref(h)), "blp_setup")
+        self._h = h
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        if stream:
+            N_.check(self.lib.blp_set_stream(h, ctypes.c_void_p(stream)), "blp_set_stream")
+
+    def close(self):
+        if self._h is not None:
+            self.lib.blp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("solver closed")
+        return self._h
+
+    def _out_like(self, a):
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                return torch.zeros_like(a)
+        except ImportError:
+            pass
+        return np.zeros(self.n)
+
+    def solve(self, f, u=None, tol=1e-10, raise_on_noconv=True):
+        """blp_solve.  u (optional) is the initial guess and is overwritten."""
+        u = self._out_like(f) if u is None else u
+        info = Info()
+        st = self.lib.blp_solve(self.handle, _ptr(f, self.n)[0], _ptr(u, self.n, True)[0], tol, ctypes.byref(info))
+        if st != N_.BLP_OK and (st != N_.BLP_ERR_NOCONV or raise_on_noconv):
+            raise BlpError(st, "blp_solve")
+        return u, info
+
+    def solve_adjoint(self, g, lam=None, tol=1e-10, raise_on_noconv=True):
+        lam = self._out_like(g) if lam is None else lam
+        info = Info()
+        st = self.lib.blp_solve_adjoint(self.handle, _ptr(g, self.n)[0], _ptr(lam, self.n, True)[0], tol,
+                                        ctypes.byref(info))
+        if st != N_.BLP_OK and (st != N_.BLP_ERR_NOCONV or raise_on_noconv):
+            raise BlpError(st, "blp_solve_adjoint")
+        return lam, info
+
+    def grad(self, u, lam):
+        outs = [self._out_like(u) for _ in range(3)]
+        N_.check(self.lib.blp_grad(self.handle, _ptr(u, self.n)[0], _ptr(lam, self.n)[0],
+                                   *[_ptr(o, self.n, True)[0] for o in outs]), "blp_grad")
+        return tuple(outs)
+
+    def apply(self, u, transpose=False):
+        y = self._out_like(u)
+        N_.check(self.lib.blp_apply_operator(self.handle, _ptr(u, self.n)[0], _ptr(y, self.n, True)[0],
+                                             int(transpose)), "blp_apply_operator")
+        return y
+
+    def precond(self, v, transpose=False, precision=BLP_FP64):
+        z = self._out_like(v)
+        cyc = ctypes.c_int(0)
+        N_.check(self.lib.blp_precond_apply(self.handle, _ptr(v, self.n)[0], _ptr(z, self.n, True)[0],
+                                            int(transpose), int(precision), ctypes.byref(cyc)), "blp_precond_apply")
+        return z, cyc.value
+
+    def kernel_launches(self):
+        return self.lib.blp_kernel_launches(self.handle)
+
+
+def solve(f, c1, c2, r, N, eps, tol=1e-10, **params):
+    """Differentiable solve u = A(c1, c2, r)^{-1} f (see autograd.BLPSolve)."""
+    from .autograd import BLPSolve
+    return BLPSolve.apply(f, c1, c2, r, N, eps, tol, params)

@@ -1,0 +1,91 @@
+"""ctypes declarations of the C ABI in include/blp.h (argument marshalling only).
+
+Every computation happens in libblp.so.  If the library is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libblp.so")
+
+BLP_OK, BLP_ERR_ARG, BLP_ERR_COEF, BLP_ERR_NOCONV, BLP_ERR_TIMEOUT, BLP_ERR_CUDA, BLP_ERR_MEM = range(7)
+BLP_FP64, BLP_MIXED = 0, 1
+BLP_STOP_SCALED, BLP_STOP_REL2, BLP_STOP_ABS2 = 0, 1, 2
+
+c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps", c_double), ("N", c_int), ("sigma", c_double), ("beta_x", c_double), ("beta_y", c_double),
+                ("restart", c_int), ("maxit", c_int), ("precision", c_int), ("stop_mode", c_int),
+                ("corner_reduction", c_double), ("corner_max_cycles", c_int), ("corner_fixed_cycles", c_int),
+                ("inner_tol", c_double), ("inner_maxit", c_int), ("check_coefficients", c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", c_int), ("iters", c_int), ("restarts", c_int), ("corner_cycles_max", c_int),
+                ("relres", c_double), ("relres_unscaled", c_double), ("t_solve_ms", c_double),
+                ("t_setup_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# exported symbol -> (restype, argtypes); the ABI test checks this against include/blp.h
+SIGNATURES = {
+    "blp_params_default": (None, [ctypes.POINTER(Params)]),
+    "blp_mesh": (c_double, [c_int, c_double, c_double, c_double, _DP]),
+    "blp_setup": (c_int, [ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]),
+    "blp_set_stream": (c_int, [c_void_p, c_void_p]),
+    "blp_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(Info)]),
+    "blp_solve_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(Info)]),
+    "blp_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "blp_apply_operator": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "blp_precond_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(c_int)]),
+    "blp_destroy": (None, [c_void_p]),
+    "blp_strerror": (ctypes.c_char_p, [c_int]),
+    "blp_kernel_launches": (c_ll, [c_void_p]),
+    # host-side layout inspection (no GPU needed)
+    "blp_layout_npad": (c_ll, [c_int]),
+    "blp_layout_addr": (c_ll, [c_int, c_int, c_int]),
+    "blp_layout_node": (c_int, [c_int, c_ll, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libblp.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    try:
+        _build.build()
+    except Exception as exc:  # no toolkit: only a prebuilt library will do
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libblp.so is not built and cannot be built here: {exc}") from exc
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class BlpError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = load().blp_strerror(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else f"{msg} (status {status})")
+
+
+def check(status, what=""):
+    if status != BLP_OK:
+        raise BlpError(status, what)
+    return status

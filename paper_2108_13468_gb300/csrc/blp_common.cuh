@@ -1,0 +1,231 @@
+// blp_common.cuh -- internal types of the GB300 solver: the region-major
+// vector layout, the handle, launch helpers.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+#include "../../include/blp.h"
+
+#define BLP_MAXLEV 24
+#define BLP_RING 256          // slots of the inter-warp handoff ring of the wavefront kernel
+#define BLP_SPIN_LIMIT (1LL << 26)
+
+// ---------------------------------------------------------------------------
+// Region-major layout.
+//
+// The interior nodes are split into the four blocks of Sec. 3.1 (C, X, Y, I).
+// Each block is stored contiguously, in the order best for the kernel that
+// sweeps it:
+//   C and I (swept by the downstream Gauss-Seidel wavefront): SKEW layout.
+//     Columns are grouped into strips of 32; inside a strip, element
+//     (a, b) (a = column, b = row, both from the block's lower-left corner)
+//     sits on "diagonal" d = (my-1-b) + 31 - (a%32) at slot (strip*D + d)*32
+//     + a%32, D = my + 31.  A warp whose lane l owns column 32s+l and runs
+//     one diagonal per step then reads 32 consecutive words per step, for
+//     the top-right-first sweep and (with d run backwards) for the
+//     bottom-left-first transposed sweep alike.  Slots that map outside the
+//     block are padding and are kept at zero in every vector.
+//   X (horizontal line solves): ROW layout, each line of constant y contiguous.
+//   Y (vertical line solves):   COL layout, each line of constant x contiguous.
+// ---------------------------------------------------------------------------
+enum { LAYOUT_SKEW = 0, LAYOUT_ROW = 1, LAYOUT_COL = 2 };
+
+struct Region {
+    int kind;
+    int mx, my;      // columns, rows
+    int i0, j0;      // global (1-based) node of local (0,0)
+    long long off;   // offset of the block inside a region-major vector
+    int S, D;        // SKEW: strips, diagonals per strip
+    long long size;  // slots (padding included)
+
+    __host__ __device__ long long addr(int a, int b) const {
+        if (kind == LAYOUT_SKEW) {
+            int s = a >> 5, l = a & 31;
+            return off + ((long long)(s * D + (my - 1 - b) + 31 - l) << 5) + l;
+        }
+        if (kind == LAYOUT_ROW) return off + (long long)b * mx + a;
+        return off + (long long)a * my + b;
+    }
+    // inverse map of a slot q (relative to off); returns false for padding
+    __host__ __device__ bool coords(long long q, int &a, int &b) const {
+        if (kind == LAYOUT_SKEW) {
+            int l = (int)(q & 31);
+            long long t = q >> 5;
+            int s = (int)(t / D), d = (int)(t % D);
+            a = s * 32 + l;
+            int ktop = d - 31 + l;
+            b = my - 1 - ktop;
+            return a < mx && ktop >= 0 && ktop < my;
+        }
+        if (kind == LAYOUT_ROW) { a = (int)(q % mx); b = (int)(q / mx); return true; }
+        a = (int)(q / my); b = (int)(q % my);
+        return true;
+    }
+};
+
+static inline Region make_region(int kind, int mx, int my, int i0, int j0, long long off) {
+    Region r;
+    r.kind = kind; r.mx = mx; r.my = my; r.i0 = i0; r.j0 = j0; r.off = off;
+    if (kind == LAYOUT_SKEW) {
+        r.S = (mx + 31) / 32; r.D = my + 31;
+        r.size = (long long)r.S * r.D * 32;
+    } else {
+        r.S = 0; r.D = 0;
+        r.size = (long long)mx * my;
+    }
+    return r;
+}
+
+struct Layout {
+    int N, L;            // intervals, L = N/2 (index of the transition node)
+    Region R[4];         // C, X, Y, I in storage order
+    long long npad;      // total slots
+
+    // global interior node (i,j), 1 <= i,j <= N-1 -> slot
+    __host__ __device__ long long addr(int i, int j) const {
+        if (i <= L) {
+            if (j <= L) return R[0].addr(i - 1, j - 1);
+            return R[1].addr(i - 1, j - L - 1);
+        }
+        if (j <= L) return R[2].addr(i - L - 1, j - 1);
+        return R[3].addr(i - L - 1, j - L - 1);
+    }
+    // slot -> global node; false for padding
+    __host__ __device__ bool node(long long p, int &i, int &j) const {
+        int k = 3;
+        if (p < R[1].off) k = 0;
+        else if (p < R[2].off) k = 1;
+        else if (p < R[3].off) k = 2;
+        int a, b;
+        if (!R[k].coords(p - R[k].off, a, b)) return false;
+        i = R[k].i0 + a;
+        j = R[k].j0 + b;
+        return true;
+    }
+};
+
+static inline Layout make_layout(int N) {
+    Layout Lt;
+    int L = N / 2;
+    Lt.N = N; Lt.L = L;
+    long long off = 0;
+    Lt.R[0] = make_region(LAYOUT_SKEW, L, L, 1, 1, off);            off += Lt.R[0].size;
+    Lt.R[1] = make_region(LAYOUT_ROW, L, N - 1 - L, 1, L + 1, off); off += Lt.R[1].size;
+    Lt.R[2] = make_region(LAYOUT_COL, N - 1 - L, L, L + 1, 1, off); off += Lt.R[2].size;
+    Lt.R[3] = make_region(LAYOUT_SKEW, N - 1 - L, N - 1 - L, L + 1, L + 1, off); off += Lt.R[3].size;
+    // keep every block 32-slot aligned (128/256-byte vector loads)
+    Lt.npad = (off + 31) & ~31LL;
+    return Lt;
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients of the row-normalised operator D^-1 A (unit diagonal) in the
+// region-major layout, for one precision.
+//   w{W,E,S,N}(i,j) = a{W,E,S,N}(i,j) / aC(i,j)     (Sec. 3 stencil)
+// Transposed-direction copies used by the adjoint sweeps:
+//   wET(i,j) = wE(i-1,j), wNT(i,j) = wN(i,j-1), wWT(i,j) = wW(i+1,j), wST(i,j) = wS(i,j+1)
+// (the couplings of row (i,j) of (D^-1 A)^T), 0 where the neighbour is outside.
+// Line factors (Thomas, Sec. 3.1 M_YY / M_XX), stored in the Y (COL) and X
+// (ROW) blocks of full-length arrays:
+//   forward   y_k = d_k + lf_k y_{k-1}
+//   backward  z_k = lg_k y_k + lh_k z_{k+1}
+// and the same for the transposed line matrices (lfT, lgT, lhT).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Coefs {
+    T *wW = nullptr, *wE = nullptr, *wS = nullptr, *wN = nullptr;
+    T *wET = nullptr, *wNT = nullptr, *wWT = nullptr, *wST = nullptr;
+    T *lf = nullptr, *lg = nullptr, *lh = nullptr;
+    T *lfT = nullptr, *lgT = nullptr, *lhT = nullptr;
+};
+
+// One level of the corner multigrid hierarchy (Sec. 3.2): a standalone
+// SKEW block (off = 0) with its own coefficient and work arrays.
+template <typename T>
+struct Level {
+    Region R;
+    T *wW = nullptr, *wE = nullptr, *wS = nullptr, *wN = nullptr;
+    T *wET = nullptr, *wNT = nullptr, *wWT = nullptr, *wST = nullptr;
+    T *omega = nullptr;   // hb*kb*aC: weight taking the normalised residual to FE scaling
+    T *dfe = nullptr;     // hb*kb
+    T *e[2] = {nullptr, nullptr};
+    T *b = nullptr;
+};
+
+template <typename T>
+struct Hierarchy {
+    int nlev = 0;
+    Level<T> lev[BLP_MAXLEV];
+};
+
+struct DevState {       // device scalars of the solver (double)
+    double red[8];      // reduction results
+    int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[2]: error code
+};
+
+struct blp_handle {
+    blp_params p;
+    int N, L;
+    Layout lay;
+    double tau_x, tau_y;
+    std::vector<double> hx, hy;     // host mesh nodes
+    double *x = nullptr, *y = nullptr;  // device mesh nodes (N+1)
+    double *aC = nullptr;           // diagonal of A, region layout (FP64)
+    double *c1 = nullptr, *c2 = nullptr, *r = nullptr;  // fields, standard layout (FP64)
+    Coefs<double> cd;
+    Coefs<float> cf;
+    Hierarchy<double> hd;
+    Hierarchy<float> hf;
+    // reduction scratch
+    double *partials = nullptr;     // [BLP_RED_BLOCKS * BLP_PART_STRIDE + 64]
+    DevState *dev = nullptr;
+    DevState *host_state = nullptr; // pinned mirror
+    int *err = nullptr;             // device error word (timeouts)
+    cudaStream_t stream = 0;
+    long long launches = 0;
+    double t_setup_ms = 0.0;
+    int last_cycles = 0;
+    // Krylov work space (allocated lazily)
+    size_t ws_bytes = 0;
+    void *ws = nullptr;
+    // standard-layout staging for host pointers
+    double *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+#define BLP_RED_BLOCKS 296    // 2 x 148: partial-sum blocks of grid reductions
+#define BLP_PART_STRIDE 65    // partial sums per block (restart + 1 <= 65)
+#define BLP_SCALARS_OFF ((long long)BLP_RED_BLOCKS * BLP_PART_STRIDE)  // 64 scalars after the partials
+
+#define CUDA_TRY(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            fprintf(stderr, "blp: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return BLP_ERR_CUDA;                                              \
+        }                                                                     \
+    } while (0)
+
+#define LAUNCH_CHECK(h)                                                       \
+    do {                                                                      \
+        (h)->launches++;                                                      \
+        cudaError_t e_ = cudaPeekAtLastError();                               \
+        if (e_ != cudaSuccess) {                                              \
+            fprintf(stderr, "blp: launch error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return BLP_ERR_CUDA;                                              \
+        }                                                                     \
+    } while (0)
+
+static inline int grid_for(long long n, int threads, int cap = 152 * 8) {
+    long long g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Internal entry points shared between translation units.
+int blp_internal_precond(blp_handle *h, const void *v, void *z, int trans, int prec, int *cycles);
+int blp_internal_ensure_ws(blp_handle *h, size_t bytes);
+int blp_internal_to_region(blp_handle *h, const double *std_in, double *reg_out, int scale_mode);
+int blp_internal_from_region(blp_handle *h, const double *reg_in, double *std_out, int scale_mode);
+template <typename T> int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles);

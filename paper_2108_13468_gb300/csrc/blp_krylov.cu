@@ -1,0 +1,624 @@
+// blp_krylov.cu -- restarted flexible GMRES (Sec. 3.3) on the row-normalised
+// system D^-1 A u = D^-1 f (D = diag(A)), the FP32-inner / FP64-refinement
+// variant, the adjoint solve and the gradient assembly; C-ABI entry points.
+#include "blp_common.cuh"
+#include <cmath>
+#include <chrono>
+#include <algorithm>
+
+#define FULL 0xffffffffu
+#define MAXV BLP_PART_STRIDE   // restart + 1 <= 65
+
+// ---------------------------------------------------------------------------
+// Operator of the normalised system (unit diagonal, Sec. 3 stencil / aC):
+//   forward  y = x + wW x_W + wE x_E + wS x_S + wN x_N
+//   adjoint  y = x + wET x_W + wWT x_E + wNT x_S + wST x_N   ((D^-1 A)^T)
+// mode 0: out = Op x;  mode 1: out = f - Op x.  Padding slots get 0.
+// ---------------------------------------------------------------------------
+template <typename T, bool TRANS>
+__global__ void k_matvec(Layout lay, Coefs<T> c, const T *__restrict__ x, T *__restrict__ out,
+                         const T *__restrict__ f, int mode) {
+    const int M = lay.N - 1;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < lay.npad; p += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        if (!lay.node(p, i, j)) { out[p] = T(0); continue; }
+        T s = x[p];
+        const T cw = TRANS ? c.wET[p] : c.wW[p];
+        const T ce = TRANS ? c.wWT[p] : c.wE[p];
+        const T cs = TRANS ? c.wNT[p] : c.wS[p];
+        const T cn = TRANS ? c.wST[p] : c.wN[p];
+        if (i > 1) s += cw * x[lay.addr(i - 1, j)];
+        if (i < M) s += ce * x[lay.addr(i + 1, j)];
+        if (j > 1) s += cs * x[lay.addr(i, j - 1)];
+        if (j < M) s += cn * x[lay.addr(i, j + 1)];
+        out[p] = mode ? f[p] - s : s;
+    }
+}
+
+// partial[blk*MAXV + i] = sum_k V_i[k] * w[k], i < nv (per-thread sums in T,
+// block sums and everything after in FP64; deterministic order)
+template <typename T>
+__global__ void __launch_bounds__(256) k_multidot(const T *__restrict__ V, long long ld, int nv,
+                                                  const T *__restrict__ w, long long n, double *partials) {
+    T acc[MAXV - 1];
+#pragma unroll
+    for (int i = 0; i < MAXV - 1; i++) acc[i] = T(0);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const T wk = w[k];
+#pragma unroll
+        for (int i = 0; i < MAXV - 1; i++)
+            if (i < nv) acc[i] += V[i * ld + k] * wk;
+    }
+    __shared__ double sh[8][MAXV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < MAXV - 1; i++) {
+        if (i < nv) {
+            double a = (double)acc[i];
+            for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(FULL, a, off);
+            if (lane == 0) sh[wid][i] = a;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) s += sh[q][threadIdx.x];
+        partials[blockIdx.x * MAXV + threadIdx.x] = s;
+    }
+}
+
+// out[i] = sum_b partials[b*MAXV + i] (+ add[i] if add), one warp per entry
+__global__ void k_reduce(const double *partials, int nb, int nv, double *out, const double *add) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x >> 5; i < nv; i += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += partials[b * MAXV + i];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(FULL, s, off);
+        if (lane == 0) out[i] = s + (add ? add[i] : 0.0);
+    }
+}
+static inline int reduce_threads(int nv) { return 32 * (nv < 32 ? nv : 32); }
+
+// w -= sum_i V_i h_i ; optional partial sums of ||w||^2 into partials[blk*MAXV]
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(const T *__restrict__ V, long long ld, int nv, const double *__restrict__ h,
+                                                T *__restrict__ w, long long n, double *partials) {
+    __shared__ T hs[MAXV];
+    if (threadIdx.x < nv) hs[threadIdx.x] = (T)h[threadIdx.x];
+    __syncthreads();
+    T acc = T(0);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        T s = w[k];
+        for (int i = 0; i < nv; i++) s -= V[i * ld + k] * hs[i];
+        w[k] = s;
+        acc += s * s;
+    }
+    if (partials) {
+        __shared__ double sh[8];
+        double a = (double)acc;
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(FULL, a, off);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); q++) s += sh[q];
+            partials[blockIdx.x * MAXV] = s;
+        }
+    }
+}
+
+// partial sums of ||x||^2 (and, with scale != null, of ||scale*x||^2 in slot 1)
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm2(const T *__restrict__ x, long long n, const double *__restrict__ scale,
+                                               double *partials) {
+    double a = 0.0, b = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double v = (double)x[k];
+        a += v * v;
+        if (scale) { double u = v * scale[k]; b += u * u; }
+    }
+    __shared__ double sh[2][8];
+    for (int off = 16; off > 0; off >>= 1) { a += __shfl_down_sync(FULL, a, off); b += __shfl_down_sync(FULL, b, off); }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = a; sh[1][threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) { s0 += sh[0][q]; s1 += sh[1][q]; }
+        partials[blockIdx.x * MAXV] = s0;
+        partials[blockIdx.x * MAXV + 1] = s1;
+    }
+}
+
+// y = alpha * x / s where s = *sdev (device scalar, sqrt applied if sq)
+template <typename TI, typename TO>
+__global__ void k_scale(const TI *__restrict__ x, TO *__restrict__ y, long long n, const double *sdev, int sq, double alpha) {
+    double s = *sdev;
+    if (sq) s = sqrt(s);
+    const double f = s != 0.0 ? alpha / s : 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        y[k] = (TO)((double)x[k] * f);
+}
+
+// u += alpha * sum_i Z_i y_i  (y on device, FP64)
+template <typename T, typename TU>
+__global__ void k_combine(const T *__restrict__ Z, long long ld, int k, const double *__restrict__ y,
+                          TU *__restrict__ u, long long n, const double *alpha_dev) {
+    __shared__ double ys[MAXV];
+    const double al = alpha_dev ? *alpha_dev : 1.0;
+    if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x] * al;
+    __syncthreads();
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; i++) s += (double)Z[i * ld + q] * ys[i];
+        u[q] = (TU)((double)u[q] + s);
+    }
+}
+
+// u += sqrt(*s2) * d   (iterative refinement step of the mixed solve)
+__global__ void k_axpy_sqrt(const float *__restrict__ d, double *__restrict__ u, long long n, const double *s2) {
+    const double a = sqrt(*s2);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        u[k] += a * (double)d[k];
+}
+
+// Device-side least-squares update (FP64): column j of the Hessenberg matrix
+// h1 + h2 (two Gram-Schmidt passes) with subdiagonal sqrt(nrm2), previous
+// Givens rotations, new rotation, residual estimate |g_{j+1}|.
+struct GivensState {
+    double H[MAXV * MAXV];   // H[i*MAXV + j], upper triangular after rotations
+    double cs[MAXV], sn[MAXV], g[MAXV + 1], y[MAXV];
+    double resid, hsub;
+};
+__global__ void k_givens(GivensState *G, int j, const double *h1, const double *h2, const double *nrm2) {
+    if (threadIdx.x != 0) return;
+    double col[MAXV + 1];
+    for (int i = 0; i <= j; i++) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
+    double hn = sqrt(*nrm2);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+        double a = col[i], b = col[i + 1];
+        col[i] = G->cs[i] * a + G->sn[i] * b;
+        col[i + 1] = -G->sn[i] * a + G->cs[i] * b;
+    }
+    double a = col[j], b = col[j + 1];
+    double d = sqrt(a * a + b * b);
+    double c = d == 0.0 ? 1.0 : a / d, s = d == 0.0 ? 0.0 : b / d;
+    G->cs[j] = c; G->sn[j] = s;
+    col[j] = d;
+    for (int i = 0; i <= j; i++) G->H[i * MAXV + j] = col[i];
+    G->g[j + 1] = -s * G->g[j];
+    G->g[j] = c * G->g[j];
+    G->resid = fabs(G->g[j + 1]);
+    G->hsub = hn;
+}
+__global__ void k_givens_init(GivensState *G, const double *beta2) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i <= MAXV; i++) G->g[i] = 0.0;
+    G->g[0] = sqrt(*beta2);
+    G->resid = G->g[0];
+}
+__global__ void k_backsolve(GivensState *G, int k) {
+    if (threadIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; i--) {
+        double s = G->g[i];
+        for (int q = i + 1; q < k; q++) s -= G->H[i * MAXV + q] * G->y[q];
+        G->y[i] = s / G->H[i * MAXV + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+template <typename T>
+struct KWork {
+    int m;
+    long long np;
+    T *V, *Z, *w;
+    double *hbuf;      // [4*MAXV]: h1, h2, norm, beta
+    GivensState *G;
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Workspace {
+    KWork<double> kd;
+    KWork<float> kf;
+    double *u, *f, *r, *t;    // FP64 region vectors
+    float *r32, *d32;
+    bool mixed;
+};
+
+static int setup_ws(blp_handle *h, Workspace &W, bool mixed) {
+    const int m = h->p.restart;
+    const long long np = h->lay.npad;
+    size_t bytes = 0;
+    auto reserve = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
+    size_t oU = reserve(sizeof(double) * np), oF = reserve(sizeof(double) * np), oR = reserve(sizeof(double) * np),
+           oT = reserve(sizeof(double) * np);
+    size_t oKd = 0, oKf = 0, oR32 = 0, oD32 = 0;
+    size_t oH = reserve(sizeof(double) * 4 * MAXV), oG = reserve(sizeof(GivensState));
+    if (!mixed) oKd = reserve(sizeof(double) * np * (2 * m + 2));
+    else {
+        oKf = reserve(sizeof(float) * np * (2 * m + 2));
+        oR32 = reserve(sizeof(float) * np);
+        oD32 = reserve(sizeof(float) * np);
+    }
+    int rc = blp_internal_ensure_ws(h, bytes);
+    if (rc) return rc;
+    char *base = (char *)h->ws;
+    CUDA_TRY(cudaMemsetAsync(base, 0, bytes, h->stream));
+    W.mixed = mixed;
+    W.u = (double *)(base + oU); W.f = (double *)(base + oF); W.r = (double *)(base + oR); W.t = (double *)(base + oT);
+    double *hb = (double *)(base + oH);
+    GivensState *G = (GivensState *)(base + oG);
+    if (!mixed) {
+        double *K = (double *)(base + oKd);
+        W.kd = {m, np, K, K + np * (m + 1), K + np * (2 * m + 1), hb, G};
+    } else {
+        float *K = (float *)(base + oKf);
+        W.kf = {m, np, K, K + np * (m + 1), K + np * (2 * m + 1), hb, G};
+        W.r32 = (float *)(base + oR32);
+        W.d32 = (float *)(base + oD32);
+    }
+    return BLP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// building blocks
+// ---------------------------------------------------------------------------
+static int nblocks(long long np) { return (int)std::min<long long>(BLP_RED_BLOCKS, std::max<long long>(1, (np + 255) / 256)); }
+
+template <typename T> static Coefs<T> &coefs(blp_handle *h);
+template <> Coefs<double> &coefs<double>(blp_handle *h) { return h->cd; }
+template <> Coefs<float> &coefs<float>(blp_handle *h) { return h->cf; }
+
+template <typename T>
+static int matvec(blp_handle *h, const T *x, T *out, const T *f, int mode, int trans) {
+    long long np = h->lay.npad;
+    if (trans) k_matvec<T, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, coefs<T>(h), x, out, f, mode);
+    else k_matvec<T, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, coefs<T>(h), x, out, f, mode);
+    LAUNCH_CHECK(h);
+    return BLP_OK;
+}
+
+// ||x||^2 (and ||scale*x||^2) -> dst[0], dst[1] (device)
+template <typename T>
+static int norm2(blp_handle *h, const T *x, const double *scale, double *dst) {
+    long long np = h->lay.npad;
+    int nb = nblocks(np);
+    k_norm2<T><<<nb, 256, 0, h->stream>>>(x, np, scale, h->partials);
+    LAUNCH_CHECK(h);
+    k_reduce<<<1, 64, 0, h->stream>>>(h->partials, nb, 2, dst, nullptr);
+    LAUNCH_CHECK(h);
+    return BLP_OK;
+}
+
+static int read_doubles(blp_handle *h, const double *src, double *dst, int n) {
+    CUDA_TRY(cudaMemcpyAsync(h->host_state->red, src, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < n; i++) dst[i] = h->host_state->red[i];
+    return BLP_OK;
+}
+
+static int check_err(blp_handle *h) {
+    int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (e) {
+        CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+        return e;
+    }
+    return BLP_OK;
+}
+
+// One FGMRES(m) run on Op x = b (Op = normalised operator or its transpose)
+// with right preconditioning by the (transposed) normalised preconditioner.
+// x: initial guess / result.  Stops when the Arnoldi estimate falls below
+// est_target (absolute), after a restart whose true residual is below
+// true_target, or at maxit.  Returns BLP_OK or BLP_ERR_NOCONV; iteration
+// counts accumulate into *iters, *restarts.
+template <typename T>
+static int fgmres(blp_handle *h, KWork<T> &K, const T *b, T *x, int trans, double est_target, double true_target,
+                  int maxit, int *iters, int *restarts, int *maxcyc, double *res_out) {
+    const long long np = K.np;
+    const int m = K.m;
+    int nb = nblocks(np);
+    int it = 0;
+    int rc;
+    double res = 0.0;
+    for (;;) {
+        // r = b - Op x -> V_0
+        if ((rc = matvec<T>(h, x, K.V, b, 1, trans))) return rc;
+        if ((rc = norm2<T>(h, K.V, nullptr, K.hbuf + 3 * MAXV))) return rc;
+        double beta2;
+        if ((rc = read_doubles(h, K.hbuf + 3 * MAXV, &beta2, 1))) return rc;
+        res = sqrt(beta2);
+        if (res <= true_target || (it >= maxit)) break;
+        (*restarts)++;
+        k_scale<T, T><<<grid_for(np, 256), 256, 0, h->stream>>>(K.V, K.V, np, K.hbuf + 3 * MAXV, 1, 1.0);
+        LAUNCH_CHECK(h);
+        k_givens_init<<<1, 32, 0, h->stream>>>(K.G, K.hbuf + 3 * MAXV);
+        LAUNCH_CHECK(h);
+        int kdim = 0;
+        bool converged = false;
+        for (int j = 0; j < m && it < maxit; j++) {
+            T *vj = K.V + j * np, *zj = K.Z + j * np;
+            int cyc = 0;
+            if ((rc = precond_apply<T>(h, vj, zj, trans, &cyc))) return rc;
+            if (cyc > *maxcyc) *maxcyc = cyc;
+            if ((rc = matvec<T>(h, zj, K.w, nullptr, 0, trans))) return rc;
+            // classical Gram-Schmidt, twice (mathematically the MGS step of Sec. 3.3)
+            int nv = j + 1;
+            double *h1 = K.hbuf, *h2 = K.hbuf + MAXV, *nr = K.hbuf + 2 * MAXV;
+            k_multidot<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
+            LAUNCH_CHECK(h);
+            k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr);
+            LAUNCH_CHECK(h);
+            k_update<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h1, K.w, np, nullptr);
+            LAUNCH_CHECK(h);
+            k_multidot<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
+            LAUNCH_CHECK(h);
+            k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr);
+            LAUNCH_CHECK(h);
+            k_update<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h2, K.w, np, h->partials);
+            LAUNCH_CHECK(h);
+            k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr);
+            LAUNCH_CHECK(h);
+            k_givens<<<1, 32, 0, h->stream>>>(K.G, j, h1, h2, nr);
+            LAUNCH_CHECK(h);
+            k_scale<T, T><<<grid_for(np, 256), 256, 0, h->stream>>>(K.w, K.V + (j + 1) * np, np, nr, 1, 1.0);
+            LAUNCH_CHECK(h);
+            it++;
+            kdim = j + 1;
+            double est[2];
+            CUDA_TRY(cudaMemcpyAsync(h->host_state->red, &K.G->resid, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+            est[0] = h->host_state->red[0];
+            est[1] = h->host_state->red[1];
+            if ((rc = check_err(h))) return rc;
+            if (est[0] <= est_target || est[1] == 0.0) { converged = true; break; }
+        }
+        k_backsolve<<<1, 32, 0, h->stream>>>(K.G, kdim);
+        LAUNCH_CHECK(h);
+        k_combine<T, T><<<grid_for(np, 256), 256, 0, h->stream>>>(K.Z, np, kdim, K.G->y, x, np, nullptr);
+        LAUNCH_CHECK(h);
+        (void)converged;
+    }
+    *iters += it;
+    if (res_out) *res_out = res;
+    return res <= true_target ? BLP_OK : BLP_ERR_NOCONV;
+}
+
+// ---------------------------------------------------------------------------
+// solves
+// ---------------------------------------------------------------------------
+static bool is_dev(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// stage a caller array (host or device) of n doubles into device memory
+static int stage_in(blp_handle *h, const double *src, int slot, const double **dst) {
+    if (is_dev(src)) { *dst = src; return BLP_OK; }
+    long long n = (long long)(h->N - 1) * (h->N - 1);
+    CUDA_TRY(cudaMemcpyAsync(h->stage[slot], src, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    *dst = h->stage[slot];
+    return BLP_OK;
+}
+
+// the forward (trans = 0) or adjoint (trans = 1) solve, FP64 or mixed
+static int solve_common(blp_handle *h, const double *f_in, double *u_io, double tol, blp_info *info, int trans) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!h || !f_in || !u_io || !(tol > 0.0)) return BLP_ERR_ARG;
+    const long long n = (long long)(h->N - 1) * (h->N - 1);
+    const long long np = h->lay.npad;
+    const bool mixed = h->p.precision == BLP_MIXED;
+    Workspace W;
+    int rc = setup_ws(h, W, mixed);
+    if (rc) return rc;
+    const double *f_dev, *u_dev_in;
+    if ((rc = stage_in(h, f_in, 0, &f_dev))) return rc;
+    bool u_is_dev = is_dev(u_io);
+    if ((rc = stage_in(h, u_io, 1, &u_dev_in))) return rc;
+    // normalised system: forward D^-1 A u = D^-1 f; adjoint (D^-1 A)^T mu = g, mu = D lambda
+    if ((rc = blp_internal_to_region(h, f_dev, W.f, trans ? 0 : 1))) return rc;
+    if ((rc = blp_internal_to_region(h, u_dev_in, W.u, trans ? 2 : 0))) return rc;
+
+    // norms of the right-hand side: scaled (slot 0) and unscaled (slot 1)
+    double *nb_dev = h->partials + BLP_SCALARS_OFF;   // scalars after the partial sums
+    if ((rc = norm2<double>(h, W.f, trans ? nullptr : h->aC, nb_dev))) return rc;
+    double fn2[2];
+    if ((rc = read_doubles(h, nb_dev, fn2, 2))) return rc;
+    double fs = sqrt(fn2[0]), fu = trans ? fs : sqrt(fn2[1]);
+    const int mode = h->p.stop_mode;
+    // target for the normalised residual
+    double target_scaled = mode == BLP_STOP_SCALED ? tol * fs : 0.0;
+    double target_unscaled = mode == BLP_STOP_REL2 ? tol * fu : (mode == BLP_STOP_ABS2 ? tol : 0.0);
+
+    int iters = 0, restarts = 0, maxcyc = 0, status = BLP_ERR_NOCONV;
+    double res_s = 0.0, res_u = 0.0;
+    // true residuals of the current u in both norms
+    auto true_res = [&](double &rs, double &ru) -> int {
+        int r2 = matvec<double>(h, W.u, W.r, W.f, 1, trans);
+        if (r2) return r2;
+        r2 = norm2<double>(h, W.r, trans ? nullptr : h->aC, nb_dev);
+        if (r2) return r2;
+        double v[2];
+        r2 = read_doubles(h, nb_dev, v, 2);
+        rs = sqrt(v[0]);
+        ru = trans ? rs : sqrt(v[1]);
+        return r2;
+    };
+    auto met = [&](double rs, double ru) {
+        return mode == BLP_STOP_SCALED ? rs <= target_scaled : ru <= target_unscaled;
+    };
+    if ((rc = true_res(res_s, res_u))) return rc;
+    if (fs == 0.0) { status = BLP_OK; }
+    else if (!mixed) {
+        int budget = h->p.maxit;
+        while (!met(res_s, res_u) && iters < budget) {
+            // the Arnoldi estimate tracks the normalised residual; for the
+            // unscaled rules convert the target with the current ratio
+            double tgt = mode == BLP_STOP_SCALED ? target_scaled : target_unscaled * (res_s / std::max(res_u, 1e-300));
+            double dummy;
+            int it0 = iters;
+            rc = fgmres<double>(h, W.kd, W.f, W.u, trans, tgt, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy);
+            if (rc != BLP_OK && rc != BLP_ERR_NOCONV) return rc;
+            if ((rc = true_res(res_s, res_u))) return rc;
+            if (iters == it0) break;
+        }
+        status = met(res_s, res_u) ? BLP_OK : BLP_ERR_NOCONV;
+    } else {
+        // FP32 inner FGMRES on Op d = r / ||r||, FP64 refinement u += ||r|| d
+        int outer = 0;
+        const int budget = h->p.maxit;
+        while (!met(res_s, res_u) && iters < budget && outer < 200) {
+            outer++;
+            restarts++;
+            k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(W.r, W.r32, np, nb_dev, 1, 1.0);
+            LAUNCH_CHECK(h);
+            CUDA_TRY(cudaMemsetAsync(W.d32, 0, sizeof(float) * np, h->stream));
+            double inner_tol = h->p.inner_tol;
+            // do not iterate the inner solve below what the outer rule needs
+            double need = mode == BLP_STOP_SCALED ? target_scaled / res_s : target_unscaled / std::max(res_u, 1e-300);
+            if (need > inner_tol) inner_tol = std::min(need * 0.5, 0.5);
+            int inner_it = 0, inner_rs = 0;
+            double ires;
+            rc = fgmres<float>(h, W.kf, W.r32, W.d32, trans, inner_tol, inner_tol,
+                               std::min(h->p.inner_maxit, budget - iters), &inner_it, &inner_rs, &maxcyc, &ires);
+            if (rc != BLP_OK && rc != BLP_ERR_NOCONV) return rc;
+            iters += inner_it;
+            // u += ||r|| d   (||r||^2 is still in nb_dev[0])
+            k_axpy_sqrt<<<grid_for(np, 256), 256, 0, h->stream>>>(W.d32, W.u, np, nb_dev);
+            LAUNCH_CHECK(h);
+            double prev = res_s;
+            if ((rc = true_res(res_s, res_u))) return rc;
+            if (!(res_s < prev)) break;   // refinement stalled
+        }
+        status = met(res_s, res_u) ? BLP_OK : BLP_ERR_NOCONV;
+    }
+    // write back
+    double *u_out_dev = u_is_dev ? u_io : h->stage[1];
+    if ((rc = blp_internal_from_region(h, W.u, u_out_dev, trans ? 1 : 0))) return rc;
+    if (!u_is_dev)
+        CUDA_TRY(cudaMemcpyAsync(u_io, u_out_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    int e = check_err(h);
+    if (e) status = e;
+    if (info) {
+        info->status = status;
+        info->iters = iters;
+        info->restarts = restarts;
+        info->corner_cycles_max = maxcyc;
+        info->relres = mode == BLP_STOP_SCALED ? (fs > 0 ? res_s / fs : 0.0)
+                                               : (mode == BLP_STOP_REL2 ? (fu > 0 ? res_u / fu : 0.0) : res_u);
+        info->relres_unscaled = fu > 0 ? res_u / fu : 0.0;
+        info->t_setup_ms = h->t_setup_ms;
+        info->t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}
+
+extern "C" int blp_solve(blp_handle *h, const double *f, double *u, double tol, blp_info *info) {
+    return solve_common(h, f, u, tol, info, 0);
+}
+extern "C" int blp_solve_adjoint(blp_handle *h, const double *g, double *lambda, double tol, blp_info *info) {
+    return solve_common(h, g, lambda, tol, info, 1);
+}
+
+// ---------------------------------------------------------------------------
+// operator / preconditioner access and the gradient
+// ---------------------------------------------------------------------------
+__global__ void k_grad(int N, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ u,
+                       const double *__restrict__ lam, double *g1, double *g2, double *gr) {
+    const int M = N - 1;
+    long long n = (long long)M * M;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k % M) + 1, j = (int)(k / M) + 1;
+        const double uk = u[k], lk = lam[k];
+        const double uE = i < M ? u[k + 1] : 0.0, uN = j < M ? u[k + M] : 0.0;
+        if (g1) g1[k] = -lk * (uk - uE) / (x[i + 1] - x[i]);
+        if (g2) g2[k] = -lk * (uk - uN) / (y[j + 1] - y[j]);
+        if (gr) gr[k] = -lk * uk;
+    }
+}
+
+extern "C" int blp_grad(blp_handle *h, const double *u, const double *lambda, double *g_c1, double *g_c2, double *g_r) {
+    if (!h || !u || !lambda) return BLP_ERR_ARG;
+    const long long n = (long long)(h->N - 1) * (h->N - 1);
+    const double *ud, *ld;
+    int rc;
+    if ((rc = stage_in(h, u, 0, &ud))) return rc;
+    if ((rc = stage_in(h, lambda, 1, &ld))) return rc;
+    double *outs[3] = {g_c1, g_c2, g_r}, *dev[3];
+    bool host[3];
+    for (int q = 0; q < 3; q++) {
+        host[q] = outs[q] && !is_dev(outs[q]);
+        dev[q] = outs[q] ? (host[q] ? nullptr : outs[q]) : nullptr;
+    }
+    // host outputs go through the remaining staging buffers, one at a time
+    for (int q = 0; q < 3; q++) {
+        double *d = dev[q];
+        if (host[q]) d = h->stage[2 + (q == 2 ? 1 : 0)];
+        if (!outs[q]) continue;
+        k_grad<<<grid_for(n, 256), 256, 0, h->stream>>>(h->N, h->x, h->y, ud, ld, q == 0 ? d : nullptr, q == 1 ? d : nullptr,
+                                                       q == 2 ? d : nullptr);
+        LAUNCH_CHECK(h);
+        if (host[q]) CUDA_TRY(cudaMemcpyAsync(outs[q], d, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    return BLP_OK;
+}
+
+extern "C" int blp_apply_operator(blp_handle *h, const double *u, double *y, int transpose) {
+    if (!h || !u || !y) return BLP_ERR_ARG;
+    const long long n = (long long)(h->N - 1) * (h->N - 1);
+    Workspace W;
+    int rc = setup_ws(h, W, false);
+    if (rc) return rc;
+    const double *ud;
+    if ((rc = stage_in(h, u, 0, &ud))) return rc;
+    // A u = D (D^-1 A) u ;  A^T u = (D^-1 A)^T (D u)
+    if ((rc = blp_internal_to_region(h, ud, W.u, transpose ? 2 : 0))) return rc;
+    if ((rc = matvec<double>(h, W.u, W.r, nullptr, 0, transpose))) return rc;
+    bool ydev = is_dev(y);
+    double *yd = ydev ? y : h->stage[2];
+    if ((rc = blp_internal_from_region(h, W.r, yd, transpose ? 0 : 2))) return rc;
+    if (!ydev) CUDA_TRY(cudaMemcpyAsync(y, yd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return BLP_OK;
+}
+
+extern "C" int blp_precond_apply(blp_handle *h, const double *v, double *z, int transpose, int precision, int *cycles) {
+    if (!h || !v || !z) return BLP_ERR_ARG;
+    const long long n = (long long)(h->N - 1) * (h->N - 1);
+    const long long np = h->lay.npad;
+    Workspace W;
+    int rc = setup_ws(h, W, precision == BLP_MIXED);
+    if (rc) return rc;
+    const double *vd;
+    if ((rc = stage_in(h, v, 0, &vd))) return rc;
+    if ((rc = blp_internal_to_region(h, vd, W.u, 0))) return rc;
+    int cyc = 0;
+    if (precision == BLP_MIXED) {
+        float *v32 = W.kf.V, *z32 = W.kf.Z;
+        double one = 1.0;
+        CUDA_TRY(cudaMemcpyAsync(W.t, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(W.u, v32, np, W.t, 0, 1.0);
+        LAUNCH_CHECK(h);
+        if ((rc = precond_apply<float>(h, v32, z32, transpose, &cyc))) return rc;
+        k_scale<float, double><<<grid_for(np, 256), 256, 0, h->stream>>>(z32, W.r, np, W.t, 0, 1.0);
+        LAUNCH_CHECK(h);
+    } else {
+        if ((rc = precond_apply<double>(h, W.u, W.r, transpose, &cyc))) return rc;
+    }
+    bool zdev = is_dev(z);
+    double *zd = zdev ? z : h->stage[2];
+    if ((rc = blp_internal_from_region(h, W.r, zd, 0))) return rc;
+    if (!zdev) CUDA_TRY(cudaMemcpyAsync(z, zd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if ((rc = check_err(h))) return rc;
+    if (cycles) *cycles = cyc;
+    return BLP_OK;
+}

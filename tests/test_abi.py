@@ -1,0 +1,76 @@
+"""The C ABI library loads without a GPU, exports every symbol declared in
+include/blp.h, and its region-major layout is a bijection (host-side checks)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2108_13468_gb300 import _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "blp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(blp_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _native.load()
+    names = declared_symbols()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _native.SIGNATURES, f"{name} has no ctypes signature"
+
+
+def test_host_only_calls():
+    lib = _native.load()
+    assert lib.blp_strerror(0) == b"ok"
+    assert b"coefficients" in lib.blp_strerror(2)
+    p = _native.Params()
+    lib.blp_params_default(ctypes.byref(p))
+    assert p.restart == 30 and p.corner_reduction == 1e3 and p.sigma == 2.0
+    import numpy as np
+    x = np.zeros(129)
+    tau = lib.blp_mesh(128, 1e-4, 2.0, 1.0, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert abs(tau - 2e-4 * np.log(128)) < 1e-18 and x[64] == tau and x[-1] == 1.0
+    assert lib.blp_mesh(127, 1e-4, 2.0, 1.0, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) < 0
+    h = ctypes.c_void_p()
+    assert lib.blp_setup(None, None, None, None, ctypes.byref(h)) == _native.BLP_ERR_ARG
+
+
+def test_library_mesh_matches_oracle_mesh():
+    import numpy as np
+    import oracle
+    for N, eps in ((64, 1e-3), (1024, 1e-8), (96, 0.3)):
+        x = np.zeros(N + 1)
+        _native.load().blp_mesh(N, eps, 2.0, 1.0, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        np.testing.assert_array_equal(x, oracle.mesh(N, eps)[0])
+
+
+@pytest.mark.parametrize("N", [8, 10, 34, 64, 66, 96, 130])
+def test_region_layout_is_a_bijection(N):
+    lib = _native.load()
+    npad = lib.blp_layout_npad(N)
+    seen = {}
+    for j in range(1, N):
+        for i in range(1, N):
+            p = lib.blp_layout_addr(N, i, j)
+            assert 0 <= p < npad
+            assert p not in seen
+            seen[p] = (i, j)
+    assert len(seen) == (N - 1) ** 2
+    ii, jj = ctypes.c_int(), ctypes.c_int()
+    valid = 0
+    for p in range(npad):
+        v = lib.blp_layout_node(N, p, ctypes.byref(ii), ctypes.byref(jj))
+        if v == 1:
+            valid += 1
+            assert seen[p] == (ii.value, jj.value)
+        else:
+            assert p not in seen
+    assert valid == (N - 1) ** 2
+    assert npad % 32 == 0
