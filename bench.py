@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-solution and unknowns/s to relative residual 1e-10 of
+the boundary-layer-preconditioned FGMRES solve, FP64 and mixed precision, on
+one GB300, with the HBM roofline of the dominant kernel.
+
+Workload (one "step"): N = 1024 intervals per axis (1 046 529 unknowns),
+eps in {1e-2, 1e-4, 1e-6, 1e-8}; c1 = 1 + x^2, c2 = 1 + y^2, r = 1 + x y,
+f = 16 seeded Fourier modes (seed 0); for each eps and each precision
+(mixed FP32/FP64, plain FP64) one blp_setup + blp_solve to relative
+residual 1e-10 of the row-normalised system.  The step's time is the sum of
+those time-to-solutions (setup included, as in the paper's timings);
+value = unknowns solved / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: independent replicas (one process per GPU, same workload each);
+value = all ranks' unknowns / max-over-ranks time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES time-to-solution & unknowns/s to rel-res 1e-10, FP64 vs mixed; HBM roofline %"
+UNIT = "unknowns/s"
+EPS_LIST = (1e-2, 1e-4, 1e-6, 1e-8)
+N_DEFAULT = 1024
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--eps", default=",".join(str(e) for e in EPS_LIST))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def build_inputs(N, eps_list):
+    import numpy as np
+    import paper_2108_13468_gb300 as blp
+    from paper_2108_13468_gb300 import inputs
+    probs = {}
+    for eps in eps_list:
+        x, _ = blp.mesh(N, eps)
+        p = inputs.problem_fourier_quadratic(x, x, N, eps, seed=0)
+        probs[eps] = [np.ascontiguousarray(a) for a in (p.c1, p.c2, p.r, p.f)]
+    return probs
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2108_13468_gb300 as blp
+    from paper_2108_13468_gb300 import _native
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = args.N
+    n = (N - 1) ** 2
+    eps_list = [float(e) for e in args.eps.split(",")]
+    precisions = ((blp.BLP_MIXED, "mixed"), (blp.BLP_FP64, "fp64"))
+    host = build_inputs(N, eps_list)
+    devin = {eps: [torch.from_numpy(a).to(dev) for a in arrs] for eps, arrs in host.items()}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+    lib = _native.load()
+
+    def one_step(record=None, profile=None):
+        """All solves of the workload; returns launches and per-solve stats."""
+        launches = 0
+        stats = []
+        for prec, pname in precisions:
+            for eps in eps_list:
+                c1, c2, r, f = devin[eps]
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+                s = blp.Solver(N, eps, c1, c2, r, precision=prec)
+                if profile is not None:
+                    lib.blp_profile(s.handle, 1)
+                u, info = s.solve(f, tol=TOL)
+                t1.record(stream)
+                if profile is not None:
+                    profile.append(read_profile(lib, s))
+                launches += s.kernel_launches()
+                s.close()
+                stats.append((pname, eps, t0, t1, info.iters, info.relres, info.corner_cycles_max))
+        return launches, stats
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        one_step()
+        flush.zero_()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, launches, per = 0.0, 0, {}
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        l, stats = one_step()
+        torch.cuda.synchronize(dev)
+        launches += l
+        for pname, eps, t0, t1, it, rr, cyc in stats:
+            ms = t0.elapsed_time(t1)
+            total_ms += ms
+            d = per.setdefault((pname, eps), {"ms": [], "iters": it, "relres": rr, "corner_cycles_max": cyc})
+            d["ms"].append(ms)
+    barrier()
+    clocks = sampler.stop()
+    step_ms = total_ms / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    units = n * len(eps_list) * len(precisions)
+    value = units * world / (step_ms * 1e-3)
+
+    # e2e: host (pinned) inputs, host output, through the public API
+    e2e = None
+    if not args.no_e2e:
+        pinned = {eps: [torch.from_numpy(a).pin_memory() for a in arrs] for eps, arrs in host.items()}
+        uh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        ms_e2e = []
+        for rep in range(2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            for prec, _ in precisions:
+                for eps in eps_list:
+                    c1, c2, r, f = pinned[eps]
+                    s = blp.Solver(N, eps, c1.numpy(), c2.numpy(), r.numpy(), precision=prec)
+                    uh.zero_()
+                    s.solve(f.numpy(), uh.numpy(), tol=TOL)
+                    s.close()
+            torch.cuda.synchronize(dev)
+            ms_e2e.append((time.perf_counter() - t) * 1e3)
+        nsolve = len(eps_list) * len(precisions)
+        e2e = {"value": units / (min(ms_e2e) * 1e-3) * world, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n * 8 * nsolve, "d2h_bytes_per_step": n * 8 * nsolve}
+
+    # instrumented replay of one step: per-kernel-class event timing
+    prof = []
+    flush.zero_()
+    one_step(profile=prof)
+    classes = merge_profiles(prof)
+    roof = roofline(classes)
+
+    detail = {}
+    for (pname, eps), d in per.items():
+        ms = statistics.mean(d["ms"])
+        detail.setdefault(pname, {})[f"{eps:g}"] = {"tts_ms": round(ms, 3), "iters": d["iters"],
+                                                     "relres": d["relres"], "corner_cycles_max": d["corner_cycles_max"],
+                                                     "unknowns_per_s": n / (ms * 1e-3)}
+    for pname in detail:
+        tot = sum(v["tts_ms"] for v in detail[pname].values())
+        detail[pname]["all"] = {"tts_ms": round(tot, 3), "unknowns_per_s": n * len(eps_list) / (tot * 1e-3)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": f"2D Shishkin N={N} ({n} unknowns), eps in {{{', '.join(f'{e:g}' for e in eps_list)}}}, "
+                                  "c1=1+x^2, c2=1+y^2, r=1+xy, 16 seeded Fourier modes; setup+FGMRES(30) to rel-res 1e-10 "
+                                  "in mixed and FP64 precision",
+                      "N": N, "eps": eps_list, "precisions": [p for _, p in precisions], "tol": TOL,
+                      "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write); working set > L2"},
+           "gpu_launches": launches // args.steps, "clocks": clocks, "e2e": e2e, "roofline": roof,
+           "detail": detail, "kernel_classes": classes}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(N)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def read_profile(lib, s):
+    import ctypes
+    from paper_2108_13468_gb300 import _native
+    res = {}
+    for c in range(lib.blp_kernel_class_count()):
+        cnt, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _native.check(lib.blp_profile_read(s.handle, c, ctypes.byref(cnt), ctypes.byref(ms), ctypes.byref(by)))
+        res[lib.blp_kernel_class_name(c).decode()] = (cnt.value, ms.value, by.value)
+    lib.blp_profile(s.handle, 0)
+    return res
+
+
+def merge_profiles(profs):
+    tot = {}
+    for p in profs:
+        for k, (c, ms, by) in p.items():
+            a = tot.setdefault(k, [0, 0.0, 0.0])
+            a[0] += c
+            a[1] += ms
+            a[2] += by
+    all_ms = sum(v[1] for v in tot.values()) or 1.0
+    return {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / all_ms, 4),
+                "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
+            for k, v in sorted(tot.items(), key=lambda kv: -kv[1][1]) if v[0] > 0}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2108_13468_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """Per-launch DRAM traffic of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*(\w+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"^\|\s*{kernel_class}\s*\|\s*([0-9.eE+]+)\s*\|", txt, re.M)
+    return float(m.group(1)) if m else None
+
+
+def roofline(classes):
+    peak, src = measured_peak()
+    if not classes:
+        return None
+    dom = next(iter(classes))   # largest device-time share
+    c = classes[dom]
+    achieved = c["GBps"] or 0.0
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": ncu_traffic(dom), "share": c["share"],
+            "note": "achieved = algorithmic bytes / CUDA-event device time of every launch of the class "
+                    "in an instrumented replay of one step"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+CPU_SAMPLE_EPS = (1e-4, 1e-6, 1e-8)
+
+
+def cpu_oracle_solve(N, eps):
+    import numpy as np
+    import oracle
+    from paper_2108_13468_gb300 import inputs
+    x, _ = oracle.mesh(N, eps)
+    p = inputs.problem_fourier_quadratic(x, x, N, eps, seed=0)
+    t = time.perf_counter()
+    A = oracle.assemble(N, eps, x, x, p.c1, p.c2, p.r)
+    P = oracle.Prec(N, eps, x, x, p.c1, p.c2, p.r)
+    u, st, it, rr, mc = oracle.fgmres(N, A, p.f, P, tol=TOL)
+    dt = time.perf_counter() - t
+    assert st == 0 and np.isfinite(u).all()
+    return dt
+
+
+def cpu_baseline(N):
+    tot = 0.0
+    for eps in CPU_SAMPLE_EPS:
+        tot += cpu_oracle_solve(N, eps)
+    n = (N - 1) ** 2
+    return {"value": n * len(CPU_SAMPLE_EPS) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle (plain C, FP64, 1 thread) setup + FGMRES(30) with the paper's preconditioner to "
+                      f"rel-res 1e-10 at N={N}, eps in {{{', '.join(f'{e:g}' for e in CPU_SAMPLE_EPS)}}} "
+                      f"({tot:.1f} s); the eps=1e-2 solve (hundreds of iterations) is left out to bound the run"}
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    N = args.N
+    n = (N - 1) ** 2
+    eps_s = CPU_SAMPLE_EPS
+    step = lambda: sum(cpu_oracle_solve(N, e) for e in eps_s)   # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
+    step_s = sum(times) / len(times)
+    value = n * len(eps_s) / step_s
+    eps = eps_s
+    sample = (f"oracle (plain C, FP64, 1 thread) setup + FGMRES(30) to rel-res 1e-10 at N={N}, "
+              f"eps in {{{', '.join(f'{e:g}' for e in eps_s)}}} per step (eps=1e-2 left out: hundreds of iterations)")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": f"2D Shishkin N={N} ({n} unknowns), oracle sample of the workload",
+                                 "N": N, "eps": list(eps), "tol": TOL},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -43,7 +43,7 @@ extern "C" {
 
 /* precision of the solve */
 #define BLP_FP64 0   /* everything in double precision */
-#define BLP_MIXED 1  /* FP32 preconditioner and inner FGMRES inside FP64 iterative refinement */
+#define BLP_MIXED 1  /* FP32 preconditioner (all block sweeps and the corner multigrid) inside FP64 FGMRES */
 
 /* stopping rules */
 #define BLP_STOP_SCALED 0   /* ||D^-1 (f - A u)||_2 <= tol ||D^-1 f||_2, D = diag(A) (default) */
@@ -65,16 +65,14 @@ typedef struct {
     double corner_reduction;   /* corner multigrid residual reduction factor (default 1e3, Sec. 3.2) */
     int corner_max_cycles;     /* cap on corner cycles per application (default 50) */
     int corner_fixed_cycles;   /* >0: exactly this many corner cycles (M becomes a fixed linear map) */
-    double inner_tol;          /* BLP_MIXED: relative tolerance of each FP32 inner solve (default 1e-5) */
-    int inner_maxit;           /* BLP_MIXED: iteration cap of each inner solve (default 300) */
     int check_coefficients;    /* nonzero: blp_setup validates c1, c2, r (default 1) */
 } blp_params;
 
 /* Statistics of the last solve. */
 typedef struct {
     int status;             /* same as the return value */
-    int iters;              /* FGMRES iterations (inner iterations for BLP_MIXED) */
-    int restarts;           /* FGMRES restart cycles (outer refinement steps for BLP_MIXED) */
+    int iters;              /* FGMRES iterations */
+    int restarts;           /* FGMRES restart cycles */
     int corner_cycles_max;  /* largest corner multigrid cycle count in any preconditioner application */
     double relres;          /* final relative residual in the stop_mode's norm (FP64, true residual) */
     double relres_unscaled; /* ||f - A u||_2 / ||f||_2 (FP64) */
@@ -84,7 +82,7 @@ typedef struct {
 
 /* Fill *p with defaults: eps = 1e-4, N = 128, sigma = 2, beta = 1, restart
  * 30, maxit 20000, FP64, scaled stopping, corner_reduction 1e3, 50 max
- * cycles, no fixed cycles, inner_tol 1e-5, inner_maxit 300, checks on. */
+ * cycles, no fixed cycles, coefficient checks on. */
 void blp_params_default(blp_params *p);
 
 /* S0. Shishkin mesh nodes (Sec. 2.2 eq. (tau 1D), Sec. 3 eq. (tau exponential)):
@@ -142,6 +140,19 @@ const char *blp_strerror(int status);
 /* Number of kernels this handle has launched since blp_setup (a counter the
  * library keeps; used to report launch counts of timed regions). */
 long long blp_kernel_launches(const blp_handle *h);
+
+/* Optional per-kernel-class timing with CUDA events on the handle's stream.
+ * blp_profile(h, 1) clears the counters and starts recording an event pair
+ * around every launch; blp_profile(h, 0) stops.  blp_profile_read returns
+ * the launch count, summed device time (ms) and summed algorithmic bytes
+ * (the words each launch must read and write once, times the word size) of
+ * class cls (0 <= cls < blp_kernel_class_count(); names from
+ * blp_kernel_class_name).  Any output pointer may be NULL.  Recording adds
+ * host overhead, so timed runs leave it off. */
+int blp_profile(blp_handle *h, int enable);
+int blp_profile_read(blp_handle *h, int cls, long long *count, double *total_ms, double *bytes);
+int blp_kernel_class_count(void);
+const char *blp_kernel_class_name(int cls);
 
 #ifdef __cplusplus
 }

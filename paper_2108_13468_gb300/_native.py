@@ -23,7 +23,7 @@ class Params(ctypes.Structure):
     _fields_ = [("eps", c_double), ("N", c_int), ("sigma", c_double), ("beta_x", c_double), ("beta_y", c_double),
                 ("restart", c_int), ("maxit", c_int), ("precision", c_int), ("stop_mode", c_int),
                 ("corner_reduction", c_double), ("corner_max_cycles", c_int), ("corner_fixed_cycles", c_int),
-                ("inner_tol", c_double), ("inner_maxit", c_int), ("check_coefficients", c_int)]
+                ("check_coefficients", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -49,6 +49,10 @@ SIGNATURES = {
     "blp_destroy": (None, [c_void_p]),
     "blp_strerror": (ctypes.c_char_p, [c_int]),
     "blp_kernel_launches": (c_ll, [c_void_p]),
+    "blp_profile": (c_int, [c_void_p, c_int]),
+    "blp_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(c_ll), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "blp_kernel_class_count": (c_int, []),
+    "blp_kernel_class_name": (ctypes.c_char_p, [c_int]),
     # host-side layout inspection (no GPU needed)
     "blp_layout_npad": (c_ll, [c_int]),
     "blp_layout_addr": (c_ll, [c_int, c_int, c_int]),

@@ -21,13 +21,15 @@
 //     Columns are grouped into strips of 32; inside a strip, element
 //     (a, b) (a = column, b = row, both from the block's lower-left corner)
 //     sits on "diagonal" d = (my-1-b) + 31 - (a%32) at slot (strip*D + d)*32
-//     + a%32, D = my + 31.  A warp whose lane l owns column 32s+l and runs
+//     + a%32, D = my + 31 rounded up to a multiple of 32.  A warp whose lane l owns column 32s+l and runs
 //     one diagonal per step then reads 32 consecutive words per step, for
 //     the top-right-first sweep and (with d run backwards) for the
 //     bottom-left-first transposed sweep alike.  Slots that map outside the
 //     block are padding and are kept at zero in every vector.
 //   X (horizontal line solves): ROW layout, each line of constant y contiguous.
 //   Y (vertical line solves):   COL layout, each line of constant x contiguous.
+// Every block starts on a 32-slot boundary (so bulk copies of a strip are
+// 16-byte aligned); the slots between blocks are padding as well.
 // ---------------------------------------------------------------------------
 enum { LAYOUT_SKEW = 0, LAYOUT_ROW = 1, LAYOUT_COL = 2 };
 
@@ -58,6 +60,7 @@ struct Region {
             b = my - 1 - ktop;
             return a < mx && ktop >= 0 && ktop < my;
         }
+        if (q >= (long long)mx * my) return false;
         if (kind == LAYOUT_ROW) { a = (int)(q % mx); b = (int)(q / mx); return true; }
         a = (int)(q / my); b = (int)(q % my);
         return true;
@@ -68,11 +71,13 @@ static inline Region make_region(int kind, int mx, int my, int i0, int j0, long 
     Region r;
     r.kind = kind; r.mx = mx; r.my = my; r.i0 = i0; r.j0 = j0; r.off = off;
     if (kind == LAYOUT_SKEW) {
-        r.S = (mx + 31) / 32; r.D = my + 31;
+        // D is padded to a multiple of 32 diagonals so the wavefront kernel
+        // can stage whole chunks of diagonals with bulk copies
+        r.S = (mx + 31) / 32; r.D = ((my + 31) + 31) / 32 * 32;
         r.size = (long long)r.S * r.D * 32;
     } else {
         r.S = 0; r.D = 0;
-        r.size = (long long)mx * my;
+        r.size = ((long long)mx * my + 31) / 32 * 32;   // keep the next block 32-slot aligned
     }
     return r;
 }
@@ -132,8 +137,14 @@ static inline Layout make_layout(int N) {
 //   backward  z_k = lg_k y_k + lh_k z_{k+1}
 // and the same for the transposed line matrices (lfT, lgT, lhT).
 // ---------------------------------------------------------------------------
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { typedef float2 type; };
+template <> struct Pair2<double> { typedef double2 type; };
+
 template <typename T>
 struct Coefs {
+    typename Pair2<T>::type *pF = nullptr;   // (wE, wN): chain couplings of the forward interior sweep
+    typename Pair2<T>::type *pR = nullptr;   // (wET, wNT): chain couplings of the reversed sweep
     T *wW = nullptr, *wE = nullptr, *wS = nullptr, *wN = nullptr;
     T *wET = nullptr, *wNT = nullptr, *wWT = nullptr, *wST = nullptr;
     T *lf = nullptr, *lg = nullptr, *lh = nullptr;
@@ -145,6 +156,8 @@ struct Coefs {
 template <typename T>
 struct Level {
     Region R;
+    typename Pair2<T>::type *pF = nullptr, *pR = nullptr;   // packed chain couplings (wE,wN) / (wET,wNT)
+    T *beta = nullptr;                                      // Gauss-Seidel right-hand side work array
     T *wW = nullptr, *wE = nullptr, *wS = nullptr, *wN = nullptr;
     T *wET = nullptr, *wNT = nullptr, *wWT = nullptr, *wST = nullptr;
     T *omega = nullptr;   // hb*kb*aC: weight taking the normalised residual to FE scaling
@@ -162,6 +175,33 @@ struct Hierarchy {
 struct DevState {       // device scalars of the solver (double)
     double red[8];      // reduction results
     int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[2]: error code
+};
+
+// Kernel classes for the optional event timing (blp_profile).
+enum {
+    KC_DTS_GS = 0,      // corner multigrid Gauss-Seidel sweeps (wavefront)
+    KC_DTS_INTERIOR,    // M_II sweep (wavefront)
+    KC_LINE_CHAIN,      // M_YY / M_XX line chains
+    KC_MG_RESTRICT,
+    KC_MG_PROLONG,
+    KC_CORNER_NORM,     // corner stopping residual + finish
+    KC_MATVEC,
+    KC_MULTIDOT,
+    KC_UPDATE,
+    KC_SMALL,           // reductions, Givens, scaling, combine
+    KC_LAYOUT,          // layout conversion, corner rhs, copies
+    KC_GS_RHS,          // parallel right-hand side of a Gauss-Seidel sweep
+    KC_COUNT
+};
+
+struct ProfState {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;   // pairs
+    std::vector<int> cls;          // class per pending pair
+    int used = 0;
+    long long count[KC_COUNT] = {0};
+    double ms[KC_COUNT] = {0.0};
+    double bytes[KC_COUNT] = {0.0};   // algorithmic bytes of the recorded launches
 };
 
 struct blp_handle {
@@ -191,6 +231,25 @@ struct blp_handle {
     void *ws = nullptr;
     // standard-layout staging for host pointers
     double *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    ProfState prof;
+};
+
+// Event timing of one launch when profiling is on (RAII around a launch).
+int blp_internal_prof_flush(blp_handle *h);
+struct ProfScope {
+    blp_handle *h;
+    int slot = -1;
+    ProfScope(blp_handle *h_, int cls, double bytes = 0.0) : h(h_) {
+        if (!h->prof.on) return;
+        h->prof.bytes[cls] += bytes;
+        if (h->prof.used * 2 + 2 > (int)h->prof.ev.size()) blp_internal_prof_flush(h);
+        slot = h->prof.used++;
+        h->prof.cls[slot] = cls;
+        cudaEventRecord(h->prof.ev[2 * slot], h->stream);
+    }
+    ~ProfScope() {
+        if (slot >= 0) cudaEventRecord(h->prof.ev[2 * slot + 1], h->stream);
+    }
 };
 
 #define BLP_RED_BLOCKS 296    // 2 x 148: partial-sum blocks of grid reductions

@@ -1,6 +1,7 @@
 // blp_krylov.cu -- restarted flexible GMRES (Sec. 3.3) on the row-normalised
-// system D^-1 A u = D^-1 f (D = diag(A)), the FP32-inner / FP64-refinement
-// variant, the adjoint solve and the gradient assembly; C-ABI entry points.
+// system D^-1 A u = D^-1 f (D = diag(A)) with the FP64 or the FP32
+// preconditioner, the adjoint solve and the gradient assembly; C-ABI entry
+// points.
 #include "blp_common.cuh"
 #include <cmath>
 #include <chrono>
@@ -15,22 +16,22 @@
 //   adjoint  y = x + wET x_W + wWT x_E + wNT x_S + wST x_N   ((D^-1 A)^T)
 // mode 0: out = Op x;  mode 1: out = f - Op x.  Padding slots get 0.
 // ---------------------------------------------------------------------------
-template <typename T, bool TRANS>
-__global__ void k_matvec(Layout lay, Coefs<T> c, const T *__restrict__ x, T *__restrict__ out,
-                         const T *__restrict__ f, int mode) {
+template <typename TC, typename TX, typename TO, bool TRANS>
+__global__ void k_matvec(Layout lay, Coefs<TC> c, const TX *__restrict__ x, TO *__restrict__ out,
+                         const TO *__restrict__ f, int mode) {
     const int M = lay.N - 1;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < lay.npad; p += (long long)gridDim.x * blockDim.x) {
         int i, j;
-        if (!lay.node(p, i, j)) { out[p] = T(0); continue; }
-        T s = x[p];
-        const T cw = TRANS ? c.wET[p] : c.wW[p];
-        const T ce = TRANS ? c.wWT[p] : c.wE[p];
-        const T cs = TRANS ? c.wNT[p] : c.wS[p];
-        const T cn = TRANS ? c.wST[p] : c.wN[p];
-        if (i > 1) s += cw * x[lay.addr(i - 1, j)];
-        if (i < M) s += ce * x[lay.addr(i + 1, j)];
-        if (j > 1) s += cs * x[lay.addr(i, j - 1)];
-        if (j < M) s += cn * x[lay.addr(i, j + 1)];
+        if (!lay.node(p, i, j)) { out[p] = TO(0); continue; }
+        TO s = (TO)x[p];
+        const TO cw = (TO)(TRANS ? c.wET[p] : c.wW[p]);
+        const TO ce = (TO)(TRANS ? c.wWT[p] : c.wE[p]);
+        const TO cs = (TO)(TRANS ? c.wNT[p] : c.wS[p]);
+        const TO cn = (TO)(TRANS ? c.wST[p] : c.wN[p]);
+        if (i > 1) s += cw * (TO)x[lay.addr(i - 1, j)];
+        if (i < M) s += ce * (TO)x[lay.addr(i + 1, j)];
+        if (j > 1) s += cs * (TO)x[lay.addr(i, j - 1)];
+        if (j < M) s += cn * (TO)x[lay.addr(i, j + 1)];
         out[p] = mode ? f[p] - s : s;
     }
 }
@@ -129,12 +130,16 @@ __global__ void __launch_bounds__(256) k_norm2(const T *__restrict__ x, long lon
     }
 }
 
-// y = alpha * x / s where s = *sdev (device scalar, sqrt applied if sq)
+// y = alpha * x / s where s = *sdev (device scalar, sqrt applied if sq);
+// sdev == nullptr: y = alpha * x (precision conversion)
 template <typename TI, typename TO>
 __global__ void k_scale(const TI *__restrict__ x, TO *__restrict__ y, long long n, const double *sdev, int sq, double alpha) {
-    double s = *sdev;
-    if (sq) s = sqrt(s);
-    const double f = s != 0.0 ? alpha / s : 0.0;
+    double f = alpha;
+    if (sdev) {
+        double s = *sdev;
+        if (sq) s = sqrt(s);
+        f = s != 0.0 ? alpha / s : 0.0;
+    }
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         y[k] = (TO)((double)x[k] * f);
 }
@@ -152,13 +157,6 @@ __global__ void k_combine(const T *__restrict__ Z, long long ld, int k, const do
         for (int i = 0; i < k; i++) s += (double)Z[i * ld + q] * ys[i];
         u[q] = (TU)((double)u[q] + s);
     }
-}
-
-// u += sqrt(*s2) * d   (iterative refinement step of the mixed solve)
-__global__ void k_axpy_sqrt(const float *__restrict__ d, double *__restrict__ u, long long n, const double *s2) {
-    const double a = sqrt(*s2);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        u[k] += a * (double)d[k];
 }
 
 // Device-side least-squares update (FP64): column j of the Hessenberg matrix
@@ -209,11 +207,17 @@ __global__ void k_backsolve(GivensState *G, int k) {
 // ---------------------------------------------------------------------------
 // workspace
 // ---------------------------------------------------------------------------
-template <typename T>
+// FGMRES work space: the basis V, the Arnoldi vector w and the solution live
+// in FP64; the preconditioned vectors Z in the preconditioner's precision TZ
+// (FP32 for the mixed solve, whose FP64 matrix-vector product reads them
+// directly, so the Arnoldi relation holds exactly for the stored Z).
+template <typename TZ>
 struct KWork {
     int m;
     long long np;
-    T *V, *Z, *w;
+    double *V, *w;
+    TZ *Z;
+    float *v32;        // mixed: FP32 copy of the vector being preconditioned
     double *hbuf;      // [4*MAXV]: h1, h2, norm, beta
     GivensState *G;
 };
@@ -224,7 +228,6 @@ struct Workspace {
     KWork<double> kd;
     KWork<float> kf;
     double *u, *f, *r, *t;    // FP64 region vectors
-    float *r32, *d32;
     bool mixed;
 };
 
@@ -235,14 +238,10 @@ static int setup_ws(blp_handle *h, Workspace &W, bool mixed) {
     auto reserve = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
     size_t oU = reserve(sizeof(double) * np), oF = reserve(sizeof(double) * np), oR = reserve(sizeof(double) * np),
            oT = reserve(sizeof(double) * np);
-    size_t oKd = 0, oKf = 0, oR32 = 0, oD32 = 0;
     size_t oH = reserve(sizeof(double) * 4 * MAXV), oG = reserve(sizeof(GivensState));
-    if (!mixed) oKd = reserve(sizeof(double) * np * (2 * m + 2));
-    else {
-        oKf = reserve(sizeof(float) * np * (2 * m + 2));
-        oR32 = reserve(sizeof(float) * np);
-        oD32 = reserve(sizeof(float) * np);
-    }
+    size_t oV = reserve(sizeof(double) * np * (m + 2));
+    size_t oZ = reserve((mixed ? sizeof(float) : sizeof(double)) * np * m);
+    size_t oV32 = reserve(sizeof(float) * np);
     int rc = blp_internal_ensure_ws(h, bytes);
     if (rc) return rc;
     char *base = (char *)h->ws;
@@ -251,15 +250,9 @@ static int setup_ws(blp_handle *h, Workspace &W, bool mixed) {
     W.u = (double *)(base + oU); W.f = (double *)(base + oF); W.r = (double *)(base + oR); W.t = (double *)(base + oT);
     double *hb = (double *)(base + oH);
     GivensState *G = (GivensState *)(base + oG);
-    if (!mixed) {
-        double *K = (double *)(base + oKd);
-        W.kd = {m, np, K, K + np * (m + 1), K + np * (2 * m + 1), hb, G};
-    } else {
-        float *K = (float *)(base + oKf);
-        W.kf = {m, np, K, K + np * (m + 1), K + np * (2 * m + 1), hb, G};
-        W.r32 = (float *)(base + oR32);
-        W.d32 = (float *)(base + oD32);
-    }
+    double *V = (double *)(base + oV);
+    if (!mixed) W.kd = {m, np, V, V + np * (m + 1), (double *)(base + oZ), (float *)(base + oV32), hb, G};
+    else W.kf = {m, np, V, V + np * (m + 1), (float *)(base + oZ), (float *)(base + oV32), hb, G};
     return BLP_OK;
 }
 
@@ -268,15 +261,15 @@ static int setup_ws(blp_handle *h, Workspace &W, bool mixed) {
 // ---------------------------------------------------------------------------
 static int nblocks(long long np) { return (int)std::min<long long>(BLP_RED_BLOCKS, std::max<long long>(1, (np + 255) / 256)); }
 
-template <typename T> static Coefs<T> &coefs(blp_handle *h);
-template <> Coefs<double> &coefs<double>(blp_handle *h) { return h->cd; }
-template <> Coefs<float> &coefs<float>(blp_handle *h) { return h->cf; }
 
-template <typename T>
-static int matvec(blp_handle *h, const T *x, T *out, const T *f, int mode, int trans) {
+// out = Op x (mode 0) or f - Op x (mode 1); FP64 operator, x in TX precision
+template <typename TX>
+static int matvec(blp_handle *h, const TX *x, double *out, const double *f, int mode, int trans) {
     long long np = h->lay.npad;
-    if (trans) k_matvec<T, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, coefs<T>(h), x, out, f, mode);
-    else k_matvec<T, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, coefs<T>(h), x, out, f, mode);
+    const double nodes = (double)(h->N - 1) * (h->N - 1);
+    ProfScope ps(h, KC_MATVEC, nodes * (sizeof(double) * (mode ? 6 : 5) + sizeof(TX)));   // x, 4 couplings, out (+ f)
+    if (trans) k_matvec<double, TX, double, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode);
+    else k_matvec<double, TX, double, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode);
     LAUNCH_CHECK(h);
     return BLP_OK;
 }
@@ -286,10 +279,12 @@ template <typename T>
 static int norm2(blp_handle *h, const T *x, const double *scale, double *dst) {
     long long np = h->lay.npad;
     int nb = nblocks(np);
-    k_norm2<T><<<nb, 256, 0, h->stream>>>(x, np, scale, h->partials);
-    LAUNCH_CHECK(h);
-    k_reduce<<<1, 64, 0, h->stream>>>(h->partials, nb, 2, dst, nullptr);
-    LAUNCH_CHECK(h);
+    { ProfScope ps_(h, KC_SMALL);
+      k_norm2<T><<<nb, 256, 0, h->stream>>>(x, np, scale, h->partials);
+      LAUNCH_CHECK(h); }
+    { ProfScope ps_(h, KC_SMALL);
+      k_reduce<<<1, 64, 0, h->stream>>>(h->partials, nb, 2, dst, nullptr);
+      LAUNCH_CHECK(h); }
     return BLP_OK;
 }
 
@@ -311,15 +306,14 @@ static int check_err(blp_handle *h) {
     return BLP_OK;
 }
 
-// One FGMRES(m) run on Op x = b (Op = normalised operator or its transpose)
-// with right preconditioning by the (transposed) normalised preconditioner.
-// x: initial guess / result.  Stops when the Arnoldi estimate falls below
-// est_target (absolute), after a restart whose true residual is below
-// true_target, or at maxit.  Returns BLP_OK or BLP_ERR_NOCONV; iteration
-// counts accumulate into *iters, *restarts.
-template <typename T>
-static int fgmres(blp_handle *h, KWork<T> &K, const T *b, T *x, int trans, double est_target, double true_target,
-                  int maxit, int *iters, int *restarts, int *maxcyc, double *res_out) {
+// Restarted FGMRES(m) on Op x = b (Op = the normalised operator or its
+// transpose) in FP64, right preconditioned by the (transposed) normalised
+// preconditioner in precision TZ.  x: initial guess / result.  Stops after
+// a restart whose true residual is <= target, or at maxit iterations (a
+// cycle also ends early when the Arnoldi estimate reaches the target).
+template <typename TZ>
+static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int trans, double target, int maxit,
+                  int *iters, int *restarts, int *maxcyc, double *res_out) {
     const long long np = K.np;
     const int m = K.m;
     int nb = nblocks(np);
@@ -328,65 +322,82 @@ static int fgmres(blp_handle *h, KWork<T> &K, const T *b, T *x, int trans, doubl
     double res = 0.0;
     for (;;) {
         // r = b - Op x -> V_0
-        if ((rc = matvec<T>(h, x, K.V, b, 1, trans))) return rc;
-        if ((rc = norm2<T>(h, K.V, nullptr, K.hbuf + 3 * MAXV))) return rc;
+        if ((rc = matvec<double>(h, x, K.V, b, 1, trans))) return rc;
+        if ((rc = norm2<double>(h, K.V, nullptr, K.hbuf + 3 * MAXV))) return rc;
         double beta2;
         if ((rc = read_doubles(h, K.hbuf + 3 * MAXV, &beta2, 1))) return rc;
         res = sqrt(beta2);
-        if (res <= true_target || (it >= maxit)) break;
+        if (res <= target || it >= maxit) break;
         (*restarts)++;
-        k_scale<T, T><<<grid_for(np, 256), 256, 0, h->stream>>>(K.V, K.V, np, K.hbuf + 3 * MAXV, 1, 1.0);
-        LAUNCH_CHECK(h);
-        k_givens_init<<<1, 32, 0, h->stream>>>(K.G, K.hbuf + 3 * MAXV);
-        LAUNCH_CHECK(h);
+        { ProfScope ps_(h, KC_SMALL);
+          k_scale<double, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.V, K.V, np, K.hbuf + 3 * MAXV, 1, 1.0);
+          LAUNCH_CHECK(h); }
+        { ProfScope ps_(h, KC_SMALL);
+          k_givens_init<<<1, 32, 0, h->stream>>>(K.G, K.hbuf + 3 * MAXV);
+          LAUNCH_CHECK(h); }
         int kdim = 0;
-        bool converged = false;
         for (int j = 0; j < m && it < maxit; j++) {
-            T *vj = K.V + j * np, *zj = K.Z + j * np;
+            double *vj = K.V + j * np;
+            TZ *zj = K.Z + j * np;
             int cyc = 0;
-            if ((rc = precond_apply<T>(h, vj, zj, trans, &cyc))) return rc;
+            if (sizeof(TZ) == sizeof(double)) {
+                if ((rc = precond_apply<TZ>(h, (const TZ *)vj, zj, trans, &cyc))) return rc;
+            } else {
+                { ProfScope ps_(h, KC_SMALL);
+                  k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(vj, K.v32, np, nullptr, 0, 1.0);
+                  LAUNCH_CHECK(h); }
+                if ((rc = precond_apply<float>(h, K.v32, (float *)zj, trans, &cyc))) return rc;
+            }
             if (cyc > *maxcyc) *maxcyc = cyc;
-            if ((rc = matvec<T>(h, zj, K.w, nullptr, 0, trans))) return rc;
+            if ((rc = matvec<TZ>(h, zj, K.w, nullptr, 0, trans))) return rc;
             // classical Gram-Schmidt, twice (mathematically the MGS step of Sec. 3.3)
             int nv = j + 1;
             double *h1 = K.hbuf, *h2 = K.hbuf + MAXV, *nr = K.hbuf + 2 * MAXV;
-            k_multidot<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
-            LAUNCH_CHECK(h);
-            k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr);
-            LAUNCH_CHECK(h);
-            k_update<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h1, K.w, np, nullptr);
-            LAUNCH_CHECK(h);
-            k_multidot<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
-            LAUNCH_CHECK(h);
-            k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr);
-            LAUNCH_CHECK(h);
-            k_update<T><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h2, K.w, np, h->partials);
-            LAUNCH_CHECK(h);
-            k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr);
-            LAUNCH_CHECK(h);
-            k_givens<<<1, 32, 0, h->stream>>>(K.G, j, h1, h2, nr);
-            LAUNCH_CHECK(h);
-            k_scale<T, T><<<grid_for(np, 256), 256, 0, h->stream>>>(K.w, K.V + (j + 1) * np, np, nr, 1, 1.0);
-            LAUNCH_CHECK(h);
+            { ProfScope ps_(h, KC_MULTIDOT, (double)np * sizeof(double) * (nv + 1));
+              k_multidot<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_SMALL);
+              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
+              k_update<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h1, K.w, np, nullptr);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_MULTIDOT, (double)np * sizeof(double) * (nv + 1));
+              k_multidot<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_SMALL);
+              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
+              k_update<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h2, K.w, np, h->partials);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_SMALL);
+              k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_SMALL);
+              k_givens<<<1, 32, 0, h->stream>>>(K.G, j, h1, h2, nr);
+              LAUNCH_CHECK(h); }
+            { ProfScope ps_(h, KC_SMALL);
+              k_scale<double, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.w, K.V + (j + 1) * np, np, nr, 1, 1.0);
+              LAUNCH_CHECK(h); }
             it++;
             kdim = j + 1;
-            double est[2];
             CUDA_TRY(cudaMemcpyAsync(h->host_state->red, &K.G->resid, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
             CUDA_TRY(cudaStreamSynchronize(h->stream));
-            est[0] = h->host_state->red[0];
-            est[1] = h->host_state->red[1];
+            const double est = h->host_state->red[0], hsub = h->host_state->red[1];
             if ((rc = check_err(h))) return rc;
-            if (est[0] <= est_target || est[1] == 0.0) { converged = true; break; }
+            if (est <= target || hsub == 0.0) break;
         }
-        k_backsolve<<<1, 32, 0, h->stream>>>(K.G, kdim);
-        LAUNCH_CHECK(h);
-        k_combine<T, T><<<grid_for(np, 256), 256, 0, h->stream>>>(K.Z, np, kdim, K.G->y, x, np, nullptr);
-        LAUNCH_CHECK(h);
-        (void)converged;
+        { ProfScope ps_(h, KC_SMALL);
+          k_backsolve<<<1, 32, 0, h->stream>>>(K.G, kdim);
+          LAUNCH_CHECK(h); }
+        { ProfScope ps_(h, KC_SMALL);
+          k_combine<TZ, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.Z, np, kdim, K.G->y, x, np, nullptr);
+          LAUNCH_CHECK(h); }
     }
     *iters += it;
     if (res_out) *res_out = res;
-    return res <= true_target ? BLP_OK : BLP_ERR_NOCONV;
+    return res <= target ? BLP_OK : BLP_ERR_NOCONV;
 }
 
 // ---------------------------------------------------------------------------
@@ -412,7 +423,6 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     auto t0 = std::chrono::steady_clock::now();
     if (!h || !f_in || !u_io || !(tol > 0.0)) return BLP_ERR_ARG;
     const long long n = (long long)(h->N - 1) * (h->N - 1);
-    const long long np = h->lay.npad;
     const bool mixed = h->p.precision == BLP_MIXED;
     Workspace W;
     int rc = setup_ws(h, W, mixed);
@@ -454,47 +464,21 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
         return mode == BLP_STOP_SCALED ? rs <= target_scaled : ru <= target_unscaled;
     };
     if ((rc = true_res(res_s, res_u))) return rc;
-    if (fs == 0.0) { status = BLP_OK; }
-    else if (!mixed) {
-        int budget = h->p.maxit;
+    if (fs == 0.0) {
+        status = BLP_OK;
+    } else {
+        const int budget = h->p.maxit;
         while (!met(res_s, res_u) && iters < budget) {
             // the Arnoldi estimate tracks the normalised residual; for the
             // unscaled rules convert the target with the current ratio
             double tgt = mode == BLP_STOP_SCALED ? target_scaled : target_unscaled * (res_s / std::max(res_u, 1e-300));
             double dummy;
             int it0 = iters;
-            rc = fgmres<double>(h, W.kd, W.f, W.u, trans, tgt, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy);
+            if (mixed) rc = fgmres<float>(h, W.kf, W.f, W.u, trans, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy);
+            else rc = fgmres<double>(h, W.kd, W.f, W.u, trans, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy);
             if (rc != BLP_OK && rc != BLP_ERR_NOCONV) return rc;
             if ((rc = true_res(res_s, res_u))) return rc;
             if (iters == it0) break;
-        }
-        status = met(res_s, res_u) ? BLP_OK : BLP_ERR_NOCONV;
-    } else {
-        // FP32 inner FGMRES on Op d = r / ||r||, FP64 refinement u += ||r|| d
-        int outer = 0;
-        const int budget = h->p.maxit;
-        while (!met(res_s, res_u) && iters < budget && outer < 200) {
-            outer++;
-            restarts++;
-            k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(W.r, W.r32, np, nb_dev, 1, 1.0);
-            LAUNCH_CHECK(h);
-            CUDA_TRY(cudaMemsetAsync(W.d32, 0, sizeof(float) * np, h->stream));
-            double inner_tol = h->p.inner_tol;
-            // do not iterate the inner solve below what the outer rule needs
-            double need = mode == BLP_STOP_SCALED ? target_scaled / res_s : target_unscaled / std::max(res_u, 1e-300);
-            if (need > inner_tol) inner_tol = std::min(need * 0.5, 0.5);
-            int inner_it = 0, inner_rs = 0;
-            double ires;
-            rc = fgmres<float>(h, W.kf, W.r32, W.d32, trans, inner_tol, inner_tol,
-                               std::min(h->p.inner_maxit, budget - iters), &inner_it, &inner_rs, &maxcyc, &ires);
-            if (rc != BLP_OK && rc != BLP_ERR_NOCONV) return rc;
-            iters += inner_it;
-            // u += ||r|| d   (||r||^2 is still in nb_dev[0])
-            k_axpy_sqrt<<<grid_for(np, 256), 256, 0, h->stream>>>(W.d32, W.u, np, nb_dev);
-            LAUNCH_CHECK(h);
-            double prev = res_s;
-            if ((rc = true_res(res_s, res_u))) return rc;
-            if (!(res_s < prev)) break;   // refinement stalled
         }
         status = met(res_s, res_u) ? BLP_OK : BLP_ERR_NOCONV;
     }
@@ -602,14 +586,14 @@ extern "C" int blp_precond_apply(blp_handle *h, const double *v, double *z, int 
     if ((rc = blp_internal_to_region(h, vd, W.u, 0))) return rc;
     int cyc = 0;
     if (precision == BLP_MIXED) {
-        float *v32 = W.kf.V, *z32 = W.kf.Z;
-        double one = 1.0;
-        CUDA_TRY(cudaMemcpyAsync(W.t, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(W.u, v32, np, W.t, 0, 1.0);
-        LAUNCH_CHECK(h);
+        float *v32 = W.kf.v32, *z32 = W.kf.Z;
+        { ProfScope ps_(h, KC_SMALL);
+          k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(W.u, v32, np, nullptr, 0, 1.0);
+          LAUNCH_CHECK(h); }
         if ((rc = precond_apply<float>(h, v32, z32, transpose, &cyc))) return rc;
-        k_scale<float, double><<<grid_for(np, 256), 256, 0, h->stream>>>(z32, W.r, np, W.t, 0, 1.0);
-        LAUNCH_CHECK(h);
+        { ProfScope ps_(h, KC_SMALL);
+          k_scale<float, double><<<grid_for(np, 256), 256, 0, h->stream>>>(z32, W.r, np, nullptr, 0, 1.0);
+          LAUNCH_CHECK(h); }
     } else {
         if ((rc = precond_apply<double>(h, W.u, W.r, transpose, &cyc))) return rc;
     }

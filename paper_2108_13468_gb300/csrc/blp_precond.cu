@@ -17,24 +17,31 @@
 //   sweep starts at the top-right node (Sec. 3.1 M_II; Sec. 3.2 smoother);
 // reversed (REV = true): zH = z(a-1,b), zV = z(a,b-1), starting bottom-left
 //   (the transposed sweeps of the adjoint).
-// GS = true makes it one Gauss-Seidel sweep of the full 5-point operator:
-//   beta = b - oH * e_old(other horizontal neighbour) - oV * e_old(other
-//   vertical neighbour), which equals the sequential sweep exactly because
-//   those neighbours come later in the sweep order.
-// One CTA, warp w owns strips in processing order w, w+W, ...; lane l owns
+// A Gauss-Seidel sweep of the full 5-point operator is this solve with
+// beta = b - (couplings to the neighbours that come later in the sweep) *
+// e_old, which k_gs_rhs forms in parallel beforehand; the result equals the
+// sequential sweep exactly because those neighbours still hold old values.
+//
+// One CTA.  Warp w owns strips in processing order w, w+W, ...; lane l owns
 // column 32s+l and handles diagonal d at step t (d = t forward, D-1-t
-// reversed).  The lane next to the previous strip ("head") takes that
-// strip's boundary column from a shared-memory ring filled by the warp that
-// processed it; all waits are bounded and report BLP_ERR_TIMEOUT.
+// reversed), so each step reads 32 consecutive words of beta and of the
+// packed (cH, cV) pairs.  Those reads are issued RP steps ahead with
+// per-lane cp.async into a shared-memory window, keeping memory latency off
+// the recurrence; the step's critical path is one shuffle and one FMA.  The
+// lane next to the previous strip ("head") takes that strip's boundary
+// column from a shared-memory ring filled by the warp that processed it.
+// All waits are bounded (BLP_ERR_TIMEOUT, no hang).
 // ---------------------------------------------------------------------------
+template <typename T> using Vec2T = Pair2<T>;
+
+#define DTS_RING 128
+
 template <typename T>
 struct DtsArgs {
     Region R;
-    const T *rhs;      // beta (plain) or b (Gauss-Seidel)
-    const T *eold;     // Gauss-Seidel: previous iterate
+    const T *beta;
+    const typename Vec2T<T>::type *pair;   // (cH, cV)
     T *out;
-    const T *cH, *cV;  // chain couplings
-    const T *oH, *oV;  // Gauss-Seidel couplings to not-yet-updated neighbours
     const T *bnd;      // reversed interior sweep: global vector with the X/Y values west/south of the block
     Layout lay;
     const int *skip;   // nonzero -> return at once (converged)
@@ -54,108 +61,260 @@ __device__ __forceinline__ bool spin_wait_ge(volatile int *ctr, int target, vola
     return true;
 }
 
-template <typename T, bool GS, bool REV>
-__global__ void __launch_bounds__(1024) k_dts(DtsArgs<T> A) {
-    if (A.skip && *A.skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *ring = reinterpret_cast<T *>(smem_raw);
-    volatile int *prod = reinterpret_cast<volatile int *>(ring + (size_t)W * BLP_RING);
-    volatile int *cons = prod + W;
-    volatile int *abort_flag = cons + W;
-    if (threadIdx.x < W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
-    if (threadIdx.x == 0) *abort_flag = 0;
-    __syncthreads();
+// --- bulk copies and mbarriers (inline PTX) --------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy (16-byte aligned, size a multiple of 16), completion on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-    const Region R = A.R;
-    const int S = R.S, D = R.D, my = R.my, mx = R.mx;
-    const int head = REV ? 0 : 31, tail = REV ? 31 : 0;
-    const int wnext = (w + 1) % W;
-    const int rounds = (S - w + W - 1) / W;
-    int in_seq = 0, out_seq = 0, cached_prod = 0, cached_cons = 0;
-
-    for (int k = 0; k < rounds; k++) {
-        const int sidx = w + k * W;
-        const int s = REV ? sidx : S - 1 - sidx;
-        const bool has_in = sidx > 0, has_out = sidx + 1 < S;
-        const int a = s * 32 + lane;
-        const long long base = R.off + (((long long)s * D) << 5) + lane;
-        T zprev = T(0);
-        for (int t = 0; t < D; t++) {
-            const int d = REV ? D - 1 - t : t;
-            const int ktop = d - 31 + lane;
-            const bool valid = (a < mx) && ktop >= 0 && ktop < my;
-            const int b = my - 1 - ktop;
-            const long long p = base + ((long long)d << 5);
-
-            T zring = T(0);
-            if (lane == head && has_in && t < my) {
-                const int seq = in_seq + t;
-                if (seq >= cached_prod) {
-                    spin_wait_ge(prod + w, seq + 1, abort_flag, A.err);
-                    cached_prod = prod[w];
-                }
-                __threadfence_block();
-                zring = ring[(size_t)w * BLP_RING + (seq % BLP_RING)];
-                if ((t & 15) == 15 || t == my - 1) {
-                    __threadfence_block();
-                    cons[w] = seq + 1;
-                }
-            }
-            T zH = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
-            if (lane == head) zH = zring;
-            T zV = zprev;
-
-            T z = T(0);
-            if (valid) {
-                if (REV && A.bnd) {
-                    if (a == 0) zH = A.bnd[A.lay.addr(R.i0 - 1, R.j0 + b)];
-                    if (b == 0) zV = A.bnd[A.lay.addr(R.i0 + a, R.j0 - 1)];
-                }
-                T beta = A.rhs[p];
-                if (GS) {
-                    const int ah = REV ? a + 1 : a - 1;
-                    const int bv = REV ? b + 1 : b - 1;
-                    if (ah >= 0 && ah < mx) beta -= A.oH[p] * A.eold[R.addr(ah, b)];
-                    if (bv >= 0 && bv < my) beta -= A.oV[p] * A.eold[R.addr(a, bv)];
-                }
-                z = beta - A.cV[p] * zV;
-                z = z - A.cH[p] * zH;
-            }
-            A.out[p] = z;
-
-            if (lane == tail && has_out) {
-                const int q = t - 31;
-                if (q >= 0 && q < my) {
-                    const int seq = out_seq + q;
-                    if (seq - cached_cons >= BLP_RING) {
-                        spin_wait_ge(cons + wnext, seq - BLP_RING + 1, abort_flag, A.err);
-                        cached_cons = cons[wnext];
-                    }
-                    ring[(size_t)wnext * BLP_RING + (seq % BLP_RING)] = z;
-                    __threadfence_block();
-                    prod[wnext] = seq + 1;
-                }
-            }
-            zprev = z;
+// bounded wait on an mbarrier phase (BLP_ERR_TIMEOUT instead of a hang)
+__device__ __forceinline__ void mbar_wait(unsigned long long *bar, unsigned parity, volatile int *abort_flag, int *err) {
+    long long n = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return;
+        if (++n > (BLP_SPIN_LIMIT >> 4)) {
+            *abort_flag = 1;
+            atomicExch(err, BLP_ERR_TIMEOUT);
+            return;
         }
-        if (has_in) in_seq += my;
-        if (has_out) out_seq += my;
     }
 }
 
-template <typename T, bool GS, bool REV>
-static int launch_dts(blp_handle *h, const DtsArgs<T> &a) {
-    int W = std::min(a.R.S, 32);
-    size_t smem = (size_t)W * BLP_RING * sizeof(T) + sizeof(int) * (2 * W + 2);
+// Shared-memory carve-up: per warp 2 stages of CH diagonals of beta (T) and
+// (cH, cV) pairs (T2), then the inter-warp ring, counters and mbarriers.
+template <typename T, int CH>
+struct DtsSmem {
+    typedef typename Vec2T<T>::type T2;
+    static constexpr size_t stage_pairs = (size_t)CH * 32 * sizeof(T2);
+    static constexpr size_t stage_beta = (size_t)CH * 32 * sizeof(T);
+    static constexpr size_t per_warp = 2 * (stage_pairs + stage_beta);
+    static size_t bytes(int W) {
+        return (size_t)W * per_warp + (size_t)W * DTS_RING * sizeof(T) + 16 * (size_t)W + 16 * (size_t)(W + 1) + 64;
+    }
+};
+
+template <typename T, bool REV, int CH, bool BND>
+__global__ void __launch_bounds__(1024) k_dts(DtsArgs<T> A) {
+    typedef typename Vec2T<T>::type T2;
+    typedef DtsSmem<T, CH> SM;
+    if (A.skip && *A.skip) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *mine = smem_raw + (size_t)w * SM::per_warp;
+    T2 *const sp0 = reinterpret_cast<T2 *>(mine);
+    T2 *const sp1 = reinterpret_cast<T2 *>(mine + SM::stage_pairs);
+    T *const sb0 = reinterpret_cast<T *>(mine + 2 * SM::stage_pairs);
+    T *const sb1 = reinterpret_cast<T *>(mine + 2 * SM::stage_pairs + SM::stage_beta);
+    unsigned char *tailp = smem_raw + (size_t)W * SM::per_warp;
+    T *ring = reinterpret_cast<T *>(tailp);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(tailp + (size_t)W * DTS_RING * sizeof(T));
+    volatile int *prod = reinterpret_cast<volatile int *>(bars + 2 * W);
+    volatile int *cons = prod + W;
+    volatile int *abort_flag = cons + W;
+    unsigned long long *const bar0 = bars + 2 * w, *const bar1 = bars + 2 * w + 1;
+    if (threadIdx.x < W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
+    if (threadIdx.x == 0) *abort_flag = 0;
+    if (lane == 0) { mbar_init(bar0, 1); mbar_init(bar1, 1); }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncthreads();
+
+    const Region R = A.R;
+    const int S = R.S, D = R.D, my = R.my;
+    const int qoff = REV ? D - (my + 31) : 0;   // padding diagonals come first in reversed order
+    const int head = REV ? 0 : 31, tail = REV ? 31 : 0;
+    const int waves = (S + W - 1) / W;
+    const int nch = D / CH;
+    const unsigned chunk_bytes = (unsigned)(SM::stage_pairs + SM::stage_beta);
+    const int wn = w + 1 < W ? w + 1 : 0;
+    T *const ring_in = ring + (size_t)w * DTS_RING;
+    T *const ring_out = ring + (size_t)wn * DTS_RING;
+    volatile int *const prod_in = prod + w;
+    volatile int *const cons_in = cons + w;
+    volatile int *const prod_out = prod + wn;
+    volatile int *const cons_out = cons + wn;
+    int in_seq = 0, out_seq = 0;
+    unsigned ph0 = 0u, ph1 = 0u;
+
+    // Strips are processed in waves of W (one per warp).  Inside a wave the
+    // boundary column passes from warp w to warp w+1 through the shared
+    // ring, a chunk of CH rows at a time; the first warp of a later wave
+    // reads the last strip of the previous wave from global memory (complete
+    // by then: the waves are separated by __syncthreads).  All waits are
+    // taken by the whole warp (uniform control flow keeps the step loop
+    // free of divergence).
+    for (int k = 0; k < waves; k++) {
+        const int sidx = w + k * W;
+        if (sidx >= S) { __syncthreads(); continue; }
+        const int s = REV ? sidx : S - 1 - sidx;
+        const bool has_in = w > 0;
+        const bool from_global = w == 0 && sidx > 0;
+        const bool has_out = (w + 1 < W) && (sidx + 1 < S);
+        const int sprev = REV ? s - 1 : s + 1;
+        const long long sbase = R.off + (((long long)s * D) << 5);
+        const T2 *const gpair = A.pair + sbase;
+        const T *const gbeta = A.beta + sbase;
+        if (lane == 0) {
+            for (int c = 0; c < 2 && c < nch; c++) {
+                const int d0 = REV ? D - (c + 1) * CH : c * CH;
+                unsigned long long *bb = c ? bar1 : bar0;
+                fence_proxy_async();
+                mbar_arrive_expect_tx(bb, chunk_bytes);
+                bulk_g2s(c ? sp1 : sp0, gpair + ((long long)d0 << 5), (unsigned)SM::stage_pairs, bb);
+                bulk_g2s(c ? sb1 : sb0, gbeta + ((long long)d0 << 5), (unsigned)SM::stage_beta, bb);
+            }
+        }
+        __syncwarp();
+        T zprev = T(0);
+        T *const outp = A.out + sbase + lane;
+        for (int c = 0; c < nch; c++) {
+            const bool st = c & 1;
+            const int t0 = c * CH;
+            // boundary inputs of this chunk (meaningful on the head lane), in registers
+            T hz[CH];
+#pragma unroll
+            for (int q = 0; q < CH; q++) hz[q] = T(0);
+            if (from_global) {
+#pragma unroll
+                for (int q = 0; q < CH; q++) {
+                    const int t = t0 + q;
+                    const int ktop = REV ? D - 1 - t - 31 : t;
+                    const int dprev = REV ? ktop : ktop + 31;
+                    if (lane == head && ktop >= 0 && ktop < my)
+                        hz[q] = A.out[R.off + (((long long)sprev * D + dprev) << 5) + (REV ? 31 : 0)];
+                }
+            }
+            mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, abort_flag, A.err);
+            if (st) ph1 ^= 1u; else ph0 ^= 1u;
+            if (has_in) {
+                const int need = min(max(t0 + CH - qoff, 0), my);
+                if (need > 0) spin_wait_ge(prod_in, in_seq + need, abort_flag, A.err);
+                __threadfence_block();
+#pragma unroll
+                for (int q = 0; q < CH; q++) {
+                    const int row = t0 + q - qoff;
+                    const T v = ring_in[(in_seq + (row < 0 ? 0 : row)) & (DTS_RING - 1)];
+                    hz[q] = (row >= 0 && row < my) ? v : T(0);
+                }
+            }
+            const T2 *const pp = st ? sp1 : sp0;
+            const T *const pb = st ? sb1 : sb0;
+            const bool is_head = lane == head;
+            T *const op = outp + ((long long)(REV ? D - 1 - t0 : t0) << 5);
+            T tz[CH];
+#pragma unroll
+            for (int q = 0; q < CH; q++) {
+                const int qi = REV ? CH - 1 - q : q;
+                const T2 cpair = pp[qi * 32 + lane];
+                const T beta = pb[qi * 32 + lane];
+                T zH = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
+                zH = is_head ? hz[q] : zH;
+                T zV = zprev;
+                if (BND) {   // reversed interior sweep: west / south neighbours in the X / Y blocks
+                    const int ktop = (REV ? D - 1 - (t0 + q) : t0 + q) - 31 + lane;
+                    const int a = s * 32 + lane, b = my - 1 - ktop;
+                    if (ktop >= 0 && ktop < my && a < R.mx) {
+                        if (a == 0) zH = A.bnd[A.lay.addr(R.i0 - 1, R.j0 + b)];
+                        if (b == 0) zV = A.bnd[A.lay.addr(R.i0 + a, R.j0 - 1)];
+                    }
+                }
+                T z = beta - cpair.y * zV;
+                z = z - cpair.x * zH;
+                op[REV ? -(q << 5) : (q << 5)] = z;
+                tz[q] = z;
+                zprev = z;
+            }
+            if (has_out) {
+                const int last = min(t0 + CH - 31 - qoff, my);
+                if (last > 0) spin_wait_ge(cons_out, out_seq + last - DTS_RING, abort_flag, A.err);
+#pragma unroll
+                for (int q = 0; q < CH; q++) {
+                    const int row = t0 + q - 31 - qoff;
+                    if (lane == tail && row >= 0 && row < my) ring_out[(out_seq + row) & (DTS_RING - 1)] = tz[q];
+                }
+                __threadfence_block();
+                if (lane == tail) *prod_out = out_seq + min(max(t0 + CH - 31 - qoff, 0), my);
+            }
+            if (has_in) {
+                __threadfence_block();
+                if (lane == head) *cons_in = in_seq + min(max(t0 + CH - qoff, 0), my);
+            }
+            __syncwarp();
+            if (lane == 0 && c + 2 < nch) {
+                const int d0 = REV ? D - (c + 3) * CH : (c + 2) * CH;
+                unsigned long long *bb = st ? bar1 : bar0;
+                fence_proxy_async();
+                mbar_arrive_expect_tx(bb, chunk_bytes);
+                bulk_g2s(st ? sp1 : sp0, gpair + ((long long)d0 << 5), (unsigned)SM::stage_pairs, bb);
+                bulk_g2s(st ? sb1 : sb0, gbeta + ((long long)d0 << 5), (unsigned)SM::stage_beta, bb);
+            }
+            __syncwarp();
+        }
+        if (has_in) in_seq += my;
+        if (has_out) out_seq += my;
+        __syncthreads();
+    }
+}
+
+template <typename T, bool REV, int CH>
+static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int W, int cls) {
+    size_t smem = DtsSmem<T, CH>::bytes(W);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_dts<T, GS, REV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_dts<T, REV, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_dts<T, REV, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
-    k_dts<T, GS, REV><<<1, W * 32, smem, h->stream>>>(a);
+    // algorithmic words per node: beta, two couplings, out
+    ProfScope ps(h, cls, (double)a.R.mx * a.R.my * sizeof(T) * 4);
+    if (a.bnd) k_dts<T, REV, CH, true><<<1, W * 32, smem, h->stream>>>(a);
+    else k_dts<T, REV, CH, false><<<1, W * 32, smem, h->stream>>>(a);
     LAUNCH_CHECK(h);
     return BLP_OK;
+}
+
+// Chunk length CH: 8 diagonals keeps the inter-warp hand-off lag short; a
+// smaller chunk where the per-warp double buffers would not fit.
+template <typename T, bool REV>
+static int launch_dts(blp_handle *h, const DtsArgs<T> &a, int cls) {
+    const int W = std::min(a.R.S, 32);
+    const size_t cap = 225 * 1024;
+    if (DtsSmem<T, 8>::bytes(W) <= cap) return launch_dts_ch<T, REV, 8>(h, a, W, cls);
+    if (DtsSmem<T, 4>::bytes(W) <= cap) return launch_dts_ch<T, REV, 4>(h, a, W, cls);
+    if (DtsSmem<T, 2>::bytes(W) <= cap) return launch_dts_ch<T, REV, 2>(h, a, W, cls);
+    return BLP_ERR_ARG;
+}
+
+// Right-hand side of one Gauss-Seidel sweep in the wavefront form:
+//   forward  beta = b - wW e_old(a-1,b) - wS e_old(a,b-1)
+//   reversed beta = b - wWT e_old(a+1,b) - wST e_old(a,b+1)
+template <typename T, bool REV>
+__global__ void k_gs_rhs(Region R, const T *__restrict__ b, const T *__restrict__ e, const T *__restrict__ oH,
+                         const T *__restrict__ oV, T *__restrict__ beta, const int *skip) {
+    if (skip && *skip) return;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < R.size; q += (long long)gridDim.x * blockDim.x) {
+        int a, bb;
+        if (!R.coords(q, a, bb)) { beta[q] = T(0); continue; }
+        T s = b[q];
+        const int ah = REV ? a + 1 : a - 1, bv = REV ? bb + 1 : bb - 1;
+        if (ah >= 0 && ah < R.mx) s -= oH[q] * e[R.addr(ah, bb)];
+        if (bv >= 0 && bv < R.my) s -= oV[q] * e[R.addr(a, bv)];
+        beta[q] = s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -307,6 +466,8 @@ static int launch_chains(blp_handle *h, const Coefs<T> &c, const T *v, T *z, con
     a.lf = TRANS ? c.lfT : c.lf; a.lg = TRANS ? c.lgT : c.lg; a.lh = TRANS ? c.lhT : c.lh;
     a.skip = skip;
     int L = h->L;
+    // per line node: v, coupling, three factors, z = 6 words
+    ProfScope ps(h, KC_LINE_CHAIN, (double)(h->lay.R[1].size + h->lay.R[2].size) * sizeof(T) * 6);
     if (L <= 4096) {
         int nt = ((L + 3) / 4 + 31) / 32 * 32;
         k_line_chain<T, 4, TRANS><<<2, nt, 0, h->stream>>>(a);
@@ -486,18 +647,26 @@ struct Cycler {
     blp_handle *h;
     Hierarchy<T> *H;
     int cur[BLP_MAXLEV];
-    const T *b0;         // level-0 right-hand side
+    bool zero[BLP_MAXLEV];   // current iterate of the level is known to be 0
+    const T *b0;             // level-0 right-hand side
     const int *skip;
 
     int gs(int l, const T *b) {
         Level<T> &Lv = H->lev[l];
+        const T *beta = b;
+        if (!zero[l]) {
+            ProfScope ps(h, KC_GS_RHS, (double)Lv.R.mx * Lv.R.my * sizeof(T) * 5);   // b, e, 2 couplings, beta
+            k_gs_rhs<T, TRANS><<<grid_for(Lv.R.size, 256), 256, 0, h->stream>>>(
+                Lv.R, b, Lv.e[cur[l]], TRANS ? Lv.wWT : Lv.wW, TRANS ? Lv.wST : Lv.wS, Lv.beta, skip);
+            LAUNCH_CHECK(h);
+            beta = Lv.beta;
+        }
         DtsArgs<T> a;
-        a.R = Lv.R; a.rhs = b; a.eold = Lv.e[cur[l]]; a.out = Lv.e[cur[l] ^ 1];
-        if (!TRANS) { a.cH = Lv.wE; a.cV = Lv.wN; a.oH = Lv.wW; a.oV = Lv.wS; }
-        else { a.cH = Lv.wET; a.cV = Lv.wNT; a.oH = Lv.wWT; a.oV = Lv.wST; }
+        a.R = Lv.R; a.beta = beta; a.pair = TRANS ? Lv.pR : Lv.pF; a.out = Lv.e[cur[l] ^ 1];
         a.bnd = nullptr; a.lay = h->lay; a.skip = skip; a.err = h->err;
-        int rc = launch_dts<T, true, TRANS>(h, a);
+        int rc = launch_dts<T, TRANS>(h, a, KC_DTS_GS);
         cur[l] ^= 1;
+        zero[l] = false;
         return rc;
     }
     int vcycle(int l) {
@@ -510,13 +679,22 @@ struct Cycler {
         int rc = gs(l, b);
         if (rc) return rc;
         Level<T> &Cn = H->lev[l + 1];
-        k_mg_restrict<T, TRANS><<<grid_for(Cn.R.size, 256), 256, 0, h->stream>>>(Lv, b, Lv.e[cur[l]], Cn, Cn.b,
-                                                                                Cn.e[cur[l + 1]], skip);
-        LAUNCH_CHECK(h);
+        {
+            // fine b, e, 4 couplings, omega once each; coarse b written
+            ProfScope ps(h, KC_MG_RESTRICT, ((double)Lv.R.mx * Lv.R.my * 7 + (double)Cn.R.mx * Cn.R.my * 2) * sizeof(T));
+            k_mg_restrict<T, TRANS><<<grid_for(Cn.R.size, 256), 256, 0, h->stream>>>(Lv, b, Lv.e[cur[l]], Cn, Cn.b,
+                                                                                    Cn.e[cur[l + 1]], skip);
+            LAUNCH_CHECK(h);
+        }
+        zero[l + 1] = true;
         rc = vcycle(l + 1);
         if (rc) return rc;
-        k_mg_prolong<T, TRANS><<<grid_for(Lv.R.size, 256), 256, 0, h->stream>>>(Lv, Lv.e[cur[l]], Cn, Cn.e[cur[l + 1]], skip);
-        LAUNCH_CHECK(h);
+        {
+            // fine e read + written, coarse e (and omega) read
+            ProfScope ps(h, KC_MG_PROLONG, ((double)Lv.R.mx * Lv.R.my * (TRANS ? 3 : 2) + (double)Cn.R.mx * Cn.R.my * (TRANS ? 2 : 1)) * sizeof(T));
+            k_mg_prolong<T, TRANS><<<grid_for(Lv.R.size, 256), 256, 0, h->stream>>>(Lv, Lv.e[cur[l]], Cn, Cn.e[cur[l + 1]], skip);
+            LAUNCH_CHECK(h);
+        }
         return gs(l, b);
     }
 };
@@ -528,7 +706,8 @@ static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out)
     Hierarchy<T> &H = hier_of<T>(h);
     Cycler<T, TRANS> cy;
     cy.h = h; cy.H = &H; cy.b0 = b0;
-    for (int l = 0; l < H.nlev; l++) cy.cur[l] = 0;
+    for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
+    cy.zero[0] = true;
     Level<T> &L0 = H.lev[0];
     CUDA_TRY(cudaMemsetAsync(L0.e[0], 0, sizeof(T) * L0.R.size, h->stream));
     const int fixed = h->p.corner_fixed_cycles;
@@ -542,10 +721,13 @@ static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out)
         const int nb = 148;
         const double red2 = h->p.corner_reduction * h->p.corner_reduction;
         cy.skip = nullptr;
-        k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
-        LAUNCH_CHECK(h);
-        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles);
-        LAUNCH_CHECK(h);
+        {
+            ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 2 * sizeof(T));
+            k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
+            LAUNCH_CHECK(h);
+            k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles);
+            LAUNCH_CHECK(h);
+        }
         cy.skip = done;
         int batch = std::max(2, std::min(h->last_cycles > 0 ? h->last_cycles : 6, h->p.corner_max_cycles));
         int enq = 0;
@@ -553,6 +735,7 @@ static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out)
             for (int c = 0; c < batch && enq < h->p.corner_max_cycles; c++, enq++) {
                 int rc = cy.vcycle(0);
                 if (rc) return rc;
+                ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 7 * sizeof(T));
                 k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[cy.cur[0]], 1, h->partials, done);
                 LAUNCH_CHECK(h);
                 k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles);
@@ -582,29 +765,36 @@ int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles) {
     if (!trans) {
         // I block: downstream Gauss-Seidel sweep of M_II (E and N kept)
         DtsArgs<T> a;
-        a.R = lay.R[3]; a.rhs = v; a.eold = nullptr; a.out = z;
-        a.cH = c.wE; a.cV = c.wN; a.oH = nullptr; a.oV = nullptr;
+        a.R = lay.R[3]; a.beta = v; a.pair = c.pF; a.out = z;
         a.bnd = nullptr; a.lay = lay; a.skip = nullptr; a.err = h->err;
-        if ((rc = launch_dts<T, false, false>(h, a))) return rc;
+        if ((rc = launch_dts<T, false>(h, a, KC_DTS_INTERIOR))) return rc;
         // Y and X blocks
         if ((rc = launch_chains<T, false>(h, c, v, z, nullptr))) return rc;
         // C block
         T *b0 = H.lev[0].b;
-        k_corner_rhs<T><<<grid_for(C.size, 256), 256, 0, h->stream>>>(lay, v, z, c.wE, c.wN, b0, nullptr);
-        LAUNCH_CHECK(h);
+        {
+            ProfScope ps(h, KC_LAYOUT);
+            k_corner_rhs<T><<<grid_for(C.size, 256), 256, 0, h->stream>>>(lay, v, z, c.wE, c.wN, b0, nullptr);
+            LAUNCH_CHECK(h);
+        }
         T *e = nullptr;
         if ((rc = corner_solve<T, false>(h, b0, &e, cycles))) return rc;
-        CUDA_TRY(cudaMemcpyAsync(z + C.off, e, sizeof(T) * C.size, cudaMemcpyDeviceToDevice, h->stream));
+        {
+            ProfScope ps(h, KC_LAYOUT);
+            CUDA_TRY(cudaMemcpyAsync(z + C.off, e, sizeof(T) * C.size, cudaMemcpyDeviceToDevice, h->stream));
+        }
     } else {
         T *e = nullptr;
         if ((rc = corner_solve<T, true>(h, v + C.off, &e, cycles))) return rc;
-        CUDA_TRY(cudaMemcpyAsync(z + C.off, e, sizeof(T) * C.size, cudaMemcpyDeviceToDevice, h->stream));
+        {
+            ProfScope ps(h, KC_LAYOUT);
+            CUDA_TRY(cudaMemcpyAsync(z + C.off, e, sizeof(T) * C.size, cudaMemcpyDeviceToDevice, h->stream));
+        }
         if ((rc = launch_chains<T, true>(h, c, v, z, nullptr))) return rc;
         DtsArgs<T> a;
-        a.R = lay.R[3]; a.rhs = v; a.eold = nullptr; a.out = z;
-        a.cH = c.wET; a.cV = c.wNT; a.oH = nullptr; a.oV = nullptr;
+        a.R = lay.R[3]; a.beta = v; a.pair = c.pR; a.out = z;
         a.bnd = z; a.lay = lay; a.skip = nullptr; a.err = h->err;
-        if ((rc = launch_dts<T, false, true>(h, a))) return rc;
+        if ((rc = launch_dts<T, true>(h, a, KC_DTS_INTERIOR))) return rc;
     }
     return BLP_OK;
 }

@@ -27,7 +27,7 @@ extern "C" void blp_params_default(blp_params *p) {
     p->eps = 1e-4; p->N = 128; p->sigma = 2.0; p->beta_x = 1.0; p->beta_y = 1.0;
     p->restart = 30; p->maxit = 20000; p->precision = BLP_FP64; p->stop_mode = BLP_STOP_SCALED;
     p->corner_reduction = 1e3; p->corner_max_cycles = 50; p->corner_fixed_cycles = 0;
-    p->inner_tol = 1e-5; p->inner_maxit = 300; p->check_coefficients = 1;
+    p->check_coefficients = 1;
 }
 
 extern "C" const char *blp_strerror(int s) {
@@ -149,6 +149,18 @@ __global__ void k_line_factors(Layout lay, const double *wW, const double *wE, c
     }
 }
 
+// (a, b) -> packed pairs, in either precision
+template <typename T>
+__global__ void k_pack_pairs(const double *__restrict__ a, const double *__restrict__ b,
+                             typename Pair2<T>::type *__restrict__ out, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        typename Pair2<T>::type v;
+        v.x = (T)a[k];
+        v.y = (T)b[k];
+        out[k] = v;
+    }
+}
+
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         b[k] = (float)a[k];
@@ -222,6 +234,8 @@ static int dalloc(T **p, long long n) {
 
 template <typename T>
 static void free_coefs(Coefs<T> &c) {
+    if (c.pF) cudaFree(c.pF);
+    if (c.pR) cudaFree(c.pR);
     T *ps[] = {c.wW, c.wE, c.wS, c.wN, c.wET, c.wNT, c.wWT, c.wST, c.lf, c.lg, c.lh, c.lfT, c.lgT, c.lhT};
     for (T *p : ps) if (p) cudaFree(p);
     c = Coefs<T>();
@@ -230,6 +244,9 @@ template <typename T>
 static void free_hier(Hierarchy<T> &H) {
     for (int l = 0; l < H.nlev; l++) {
         Level<T> &v = H.lev[l];
+        if (v.pF) cudaFree(v.pF);
+        if (v.pR) cudaFree(v.pR);
+        if (v.beta) cudaFree(v.beta);
         T *ps[] = {v.wW, v.wE, v.wS, v.wN, v.wET, v.wNT, v.wWT, v.wST, v.omega, v.dfe, v.e[0], v.e[1], v.b};
         for (T *p : ps) if (p) cudaFree(p);
         v = Level<T>();
@@ -244,6 +261,8 @@ extern "C" void blp_destroy(blp_handle *h) {
     free_coefs(h->cf);
     free_hier(h->hd);
     free_hier(h->hf);
+    blp_internal_prof_flush(h);
+    for (auto &e : h->prof.ev) cudaEventDestroy(e);
     void *ps[] = {h->x, h->y, h->aC, h->c1, h->c2, h->r, h->partials, h->dev, h->err, h->ws,
                   h->stage[0], h->stage[1], h->stage[2], h->stage[3]};
     for (void *p : ps) if (p) cudaFree(p);
@@ -258,6 +277,61 @@ extern "C" int blp_set_stream(blp_handle *h, void *stream) {
 }
 
 extern "C" long long blp_kernel_launches(const blp_handle *h) { return h ? h->launches : -1; }
+
+int blp_internal_prof_flush(blp_handle *h) {
+    ProfState &P = h->prof;
+    if (P.used == 0) return BLP_OK;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < P.used; i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]) == cudaSuccess) {
+            P.count[P.cls[i]]++;
+            P.ms[P.cls[i]] += ms;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    P.used = 0;
+    return BLP_OK;
+}
+
+extern "C" int blp_profile(blp_handle *h, int enable) {
+    if (!h) return BLP_ERR_ARG;
+    ProfState &P = h->prof;
+    if (enable) {
+        if (P.ev.empty()) {
+            P.ev.resize(2 * 4096);
+            P.cls.resize(4096);
+            for (auto &e : P.ev) CUDA_TRY(cudaEventCreate(&e));
+        }
+        for (int c = 0; c < KC_COUNT; c++) { P.count[c] = 0; P.ms[c] = 0.0; P.bytes[c] = 0.0; }
+        P.used = 0;
+        P.on = true;
+    } else {
+        int rc = blp_internal_prof_flush(h);
+        P.on = false;
+        return rc;
+    }
+    return BLP_OK;
+}
+
+extern "C" int blp_profile_read(blp_handle *h, int cls, long long *count, double *total_ms, double *bytes) {
+    if (!h || cls < 0 || cls >= KC_COUNT) return BLP_ERR_ARG;
+    int rc = blp_internal_prof_flush(h);
+    if (rc) return rc;
+    if (count) *count = h->prof.count[cls];
+    if (total_ms) *total_ms = h->prof.ms[cls];
+    if (bytes) *bytes = h->prof.bytes[cls];
+    return BLP_OK;
+}
+
+extern "C" int blp_kernel_class_count(void) { return KC_COUNT; }
+
+extern "C" const char *blp_kernel_class_name(int cls) {
+    static const char *names[KC_COUNT] = {"dts_gs", "dts_interior", "line_chain", "mg_restrict", "mg_prolong",
+                                          "corner_norm", "matvec", "multidot", "update", "small", "layout", "gs_rhs"};
+    return (cls >= 0 && cls < KC_COUNT) ? names[cls] : "";
+}
 
 int blp_internal_ensure_ws(blp_handle *h, size_t bytes) {
     if (h->ws_bytes >= bytes) return BLP_OK;
@@ -291,7 +365,21 @@ static int alloc_coefs(Coefs<T> &c, long long n) {
     return BLP_OK;
 }
 
+template <typename T>
+static int make_pairs(blp_handle *h, const double *wE, const double *wN, const double *wET, const double *wNT,
+                      typename Pair2<T>::type **pF, typename Pair2<T>::type **pR, long long n) {
+    TRY(dalloc(pF, n));
+    TRY(dalloc(pR, n));
+    k_pack_pairs<T><<<grid_for(n, 256), 256, 0, h->stream>>>(wE, wN, *pF, n);
+    LAUNCH_CHECK(h);
+    k_pack_pairs<T><<<grid_for(n, 256), 256, 0, h->stream>>>(wET, wNT, *pR, n);
+    LAUNCH_CHECK(h);
+    return BLP_OK;
+}
+
 static int convert_coefs(blp_handle *h, long long n) {
+    TRY(make_pairs<double>(h, h->cd.wE, h->cd.wN, h->cd.wET, h->cd.wNT, &h->cd.pF, &h->cd.pR, n));
+    TRY(make_pairs<float>(h, h->cd.wE, h->cd.wN, h->cd.wET, h->cd.wNT, &h->cf.pF, &h->cf.pR, n));
     double *src[] = {h->cd.wW, h->cd.wE, h->cd.wS, h->cd.wN, h->cd.wET, h->cd.wNT, h->cd.wWT, h->cd.wST,
                      h->cd.lf, h->cd.lg, h->cd.lh, h->cd.lfT, h->cd.lgT, h->cd.lhT};
     float *dst[] = {h->cf.wW, h->cf.wE, h->cf.wS, h->cf.wN, h->cf.wET, h->cf.wNT, h->cf.wWT, h->cf.wST,
@@ -360,6 +448,12 @@ static int build_hierarchy(blp_handle *h) {
             k_to_float<<<grid_for(n, 256), 256, 0, h->stream>>>(*pd[q], *pf[q], n);
             LAUNCH_CHECK(h);
         }
+        TRY(make_pairs<double>(h, D.wE, D.wN, D.wET, D.wNT, &D.pF, &D.pR, n));
+        TRY(make_pairs<float>(h, D.wE, D.wN, D.wET, D.wNT, &F.pF, &F.pR, n));
+        TRY(dalloc(&D.beta, n));
+        TRY(dalloc(&F.beta, n));
+        CUDA_TRY(cudaMemset(D.beta, 0, sizeof(double) * n));
+        CUDA_TRY(cudaMemset(F.beta, 0, sizeof(float) * n));
         CUDA_TRY(cudaStreamSynchronize(h->stream));
     }
     cudaFree(dxs);

@@ -122,8 +122,10 @@ def test_edge_cases_and_errors():
     bad[5] = np.nan
     with pytest.raises(blp.BlpError):
         blp.Solver(N, eps, T(p.c1), T(p.c2), T(bad))
-    with pytest.raises(blp.BlpError):
-        blp.Solver(63, eps, T(p.c1), T(p.c2), T(p.r))
+    one = T(np.ones(62 * 62))
+    with pytest.raises(blp.BlpError) as e:
+        blp.Solver(63, eps, one, one, one)                         # odd N: rejected by blp_setup
+    assert e.value.status == blp._native.BLP_ERR_ARG
 
 
 @pytest.mark.parametrize("eps", [1e-4, 1e-8])
