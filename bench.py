@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--eps", default=",".join(str(e) for e in EPS_LIST))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "precond", "solve"],
+                    help="precond/solve: a short fixed run for profiling under ncu (no JSON line)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="for --mode precond/solve")
     return ap.parse_args()
 
 
@@ -390,9 +393,32 @@ def run_reference(args):
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_profile_target(args):
+    """Short fixed workload for ncu: setup on the first eps of --eps, then two
+    preconditioner applications (--mode precond) or one solve (--mode solve)."""
+    import numpy as np
+    import torch
+    import paper_2108_13468_gb300 as blp
+    dev = torch.device("cuda", 0)
+    N, eps = args.N, float(args.eps.split(",")[0])
+    prec = blp.BLP_MIXED if args.precision == "mixed" else blp.BLP_FP64
+    c1, c2, r, f = [torch.from_numpy(a).to(dev) for a in build_inputs(N, [eps])[eps]]
+    s = blp.Solver(N, eps, c1, c2, r, precision=prec)
+    if args.mode == "precond":
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal((N - 1) ** 2)).to(dev)
+        for _ in range(2):
+            s.precond(v, precision=prec)
+    else:
+        s.solve(f, tol=TOL)
+    torch.cuda.synchronize()
+    print(f"profile target done: mode={args.mode} N={N} eps={eps:g} precision={args.precision}")
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode != "bench":
+        run_profile_target(a)
     else:
         run_ours(a)
