@@ -52,9 +52,10 @@ struct Region {
     // inverse map of a slot q (relative to off); returns false for padding
     __host__ __device__ bool coords(long long q, int &a, int &b) const {
         if (kind == LAYOUT_SKEW) {
-            int l = (int)(q & 31);
-            long long t = q >> 5;
-            int s = (int)(t / D), d = (int)(t % D);
+            // slot counts stay far below 2^36, so the strip/diagonal split fits 32-bit arithmetic
+            const int l = (int)(q & 31);
+            const int t = (int)(q >> 5);
+            const int s = t / D, d = t - s * D;
             a = s * 32 + l;
             int ktop = d - 31 + l;
             b = my - 1 - ktop;
@@ -164,7 +165,12 @@ struct Level {
     T *dfe = nullptr;     // hb*kb
     T *e[2] = {nullptr, nullptr};
     T *b = nullptr;
+    // natural (row-major m x m) copies for the fused coarse-level kernel, 10 arrays of m*m:
+    // wW, wE, wS, wN, wET, wWT, wNT, wST, omega, dfe   (levels with m <= BLP_COARSE_MAX)
+    T *nat = nullptr;
 };
+
+#define BLP_COARSE_MAX 128
 
 template <typename T>
 struct Hierarchy {
@@ -174,7 +180,7 @@ struct Hierarchy {
 
 struct DevState {       // device scalars of the solver (double)
     double red[8];      // reduction results
-    int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[2]: error code
+    int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[3]: running max of cycles
 };
 
 // Kernel classes for the optional event timing (blp_profile).
@@ -191,6 +197,7 @@ enum {
     KC_SMALL,           // reductions, Givens, scaling, combine
     KC_LAYOUT,          // layout conversion, corner rhs, copies
     KC_GS_RHS,          // parallel right-hand side of a Gauss-Seidel sweep
+    KC_MG_COARSE,       // fused coarse levels of the corner multigrid
     KC_COUNT
 };
 

@@ -463,6 +463,7 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     auto met = [&](double rs, double ru) {
         return mode == BLP_STOP_SCALED ? rs <= target_scaled : ru <= target_unscaled;
     };
+    CUDA_TRY(cudaMemsetAsync(&h->dev->flags[3], 0, sizeof(int), h->stream));
     if ((rc = true_res(res_s, res_u))) return rc;
     if (fs == 0.0) {
         status = BLP_OK;
@@ -490,6 +491,11 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     int e = check_err(h);
     if (e) status = e;
+    {
+        int devmax = 0;
+        CUDA_TRY(cudaMemcpy(&devmax, &h->dev->flags[3], sizeof(int), cudaMemcpyDeviceToHost));
+        if (devmax > maxcyc) maxcyc = devmax;
+    }
     if (info) {
         info->status = status;
         info->iters = iters;
@@ -596,6 +602,10 @@ extern "C" int blp_precond_apply(blp_handle *h, const double *v, double *z, int 
           LAUNCH_CHECK(h); }
     } else {
         if ((rc = precond_apply<double>(h, W.u, W.r, transpose, &cyc))) return rc;
+    }
+    if (cyc < 0) {   // counted on the device by the fused corner kernel
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        CUDA_TRY(cudaMemcpy(&cyc, &h->dev->flags[1], sizeof(int), cudaMemcpyDeviceToHost));
     }
     bool zdev = is_dev(z);
     double *zd = zdev ? z : h->stage[2];

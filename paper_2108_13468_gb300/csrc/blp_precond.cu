@@ -7,6 +7,7 @@
 //                      smoother + fused restriction / prolongation kernels
 #include "blp_common.cuh"
 #include <algorithm>
+#include <cstring>
 
 #define FULL 0xffffffffu
 
@@ -275,8 +276,11 @@ static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int W, int cls) {
     size_t smem = DtsSmem<T, CH>::bytes(W);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_dts<T, REV, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(k_dts<T, REV, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (cudaFuncSetAttribute(k_dts<T, REV, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess ||
+            cudaFuncSetAttribute(k_dts<T, REV, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return BLP_ERR_CUDA;
+        }
         attr_set = true;
     }
     // algorithmic words per node: beta, two couplings, out
@@ -321,6 +325,8 @@ __global__ void k_gs_rhs(Region R, const T *__restrict__ b, const T *__restrict_
 // Block-wide scan of an affine recurrence x_e = alpha_e + mu_e x_{e-1}
 // (BACK = false, e ascending) or x_e = alpha_e + mu_e x_{e+1} (BACK = true),
 // x = 0 outside the sequence.  Thread t owns elements [t*KPT, t*KPT+KPT).
+// Warp-level Kogge-Stone over the per-thread compositions, then the warp
+// totals are composed serially (few warps) through shared memory.
 // ---------------------------------------------------------------------------
 template <typename T, int KPT, bool BACK>
 __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&mu)[KPT], T (&x)[KPT], T *sh) {
@@ -332,37 +338,25 @@ __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&
         A = al[e] + mu[e] * A;
         M = mu[e] * M;
     }
-    // inclusive scan over lanes in sequence order (ascending lanes forward,
-    // descending lanes backward)
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        T Ap = BACK ? __shfl_down_sync(FULL, A, off) : __shfl_up_sync(FULL, A, off);
-        T Mp = BACK ? __shfl_down_sync(FULL, M, off) : __shfl_up_sync(FULL, M, off);
+        const T Ap = BACK ? __shfl_down_sync(FULL, A, off) : __shfl_up_sync(FULL, A, off);
+        const T Mp = BACK ? __shfl_down_sync(FULL, M, off) : __shfl_up_sync(FULL, M, off);
         const bool ok = BACK ? (lane + off < 32) : (lane >= off);
         if (ok) { A = A + M * Ap; M = M * Mp; }
     }
     const int last = BACK ? 0 : 31;
     if (lane == last) { sh[wid] = A; sh[32 + wid] = M; }
     __syncthreads();
-    // carry into this warp: compose the totals of the warps before it
+    // carry into this warp: composition of the warps before it in sequence order
     T carry = T(0);
-    {
-        const int src = BACK ? nw - 1 - lane : lane;   // sequence position -> warp id
-        T Aw = (lane < nw) ? sh[src] : T(0);
-        T Mw = (lane < nw) ? sh[32 + src] : T(1);
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            T Ap = __shfl_up_sync(FULL, Aw, off);
-            T Mp = __shfl_up_sync(FULL, Mw, off);
-            if (lane >= off) { Aw = Aw + Mw * Ap; Mw = Mw * Mp; }
-        }
-        const int pos = BACK ? nw - 1 - wid : wid;     // this warp's position in sequence order
-        T c = __shfl_sync(FULL, Aw, (pos + 31) & 31);
-        carry = pos > 0 ? c : T(0);
+    if (BACK) {
+        for (int v = nw - 1; v > wid; v--) carry = sh[v] + sh[32 + v] * carry;
+    } else {
+        for (int v = 0; v < wid; v++) carry = sh[v] + sh[32 + v] * carry;
     }
-    __syncthreads();
-    T Aprev = BACK ? __shfl_down_sync(FULL, A, 1) : __shfl_up_sync(FULL, A, 1);
-    T Mprev = BACK ? __shfl_down_sync(FULL, M, 1) : __shfl_up_sync(FULL, M, 1);
+    const T Aprev = BACK ? __shfl_down_sync(FULL, A, 1) : __shfl_up_sync(FULL, A, 1);
+    const T Mprev = BACK ? __shfl_down_sync(FULL, M, 1) : __shfl_up_sync(FULL, M, 1);
     const bool first = BACK ? (lane == 31) : (lane == 0);
     T xin = first ? carry : Aprev + Mprev * carry;
 #pragma unroll
@@ -371,6 +365,7 @@ __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&
         xin = al[e] + mu[e] * xin;
         x[e] = xin;
     }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +376,9 @@ __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&
 // into I).  TRANS: the transposed block solves (Y left to right, X bottom up)
 // with the couplings from the line before or, for the first line, from C.
 // Both blocks run in one launch.  Each line: Thomas with the stored factors,
-// both sweeps as block-wide affine scans.
+// both sweeps as block-wide affine scans.  The next line's data (right-hand
+// side, coupling, factors, boundary value) is loaded while the current line
+// is solved, so only the scans stay on the chain's critical path.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct ChainArgs {
@@ -393,60 +390,76 @@ struct ChainArgs {
     const int *skip;
 };
 
+template <typename T, int KPT>
+struct LineData {
+    T v[KPT], c[KPT], f[KPT], g[KPT], h[KPT], prev[KPT];
+    T bval;   // boundary value (I neighbour of the last node; forward only)
+};
+
 template <typename T, int KPT, bool TRANS>
-__global__ void __launch_bounds__(1024) k_line_chain(ChainArgs<T> A) {
+__device__ __forceinline__ void load_line(const ChainArgs<T> &A, bool isY, int nlines, int li, int e0,
+                                          LineData<T, KPT> &D) {
+    const Layout &lay = A.lay;
+    const int L = lay.L;
+    const Region &C = lay.R[0], &I = lay.R[3];
+    const Region &B = isY ? lay.R[2] : lay.R[1];
+    const int line = TRANS ? li : nlines - 1 - li;
+    const long long base = B.off + (long long)line * L;
+#pragma unroll
+    for (int q = 0; q < KPT; q++) {
+        const int e = e0 + q;
+        if (e < L) {
+            const long long s = base + e;
+            D.v[q] = A.v[s];
+            D.c[q] = TRANS ? (isY ? A.wET[s] : A.wNT[s]) : (isY ? A.wE[s] : A.wN[s]);
+            D.f[q] = A.lf[s];
+            D.g[q] = A.lg[s];
+            D.h[q] = A.lh[s];
+            D.prev[q] = (TRANS && li == 0) ? A.z[isY ? C.addr(L - 1, e) : C.addr(e, L - 1)] : T(0);
+        } else {
+            D.v[q] = T(0); D.c[q] = T(0); D.f[q] = T(1); D.g[q] = T(0); D.h[q] = T(1); D.prev[q] = T(0);
+        }
+    }
+    D.bval = T(0);
+    if (!TRANS && e0 <= L - 1 && L - 1 < e0 + KPT) {
+        const long long s = base + (L - 1);
+        const long long pi = isY ? I.addr(line, 0) : I.addr(0, line);
+        D.bval = (isY ? A.wN[s] : A.wE[s]) * A.z[pi];
+    }
+}
+
+template <typename T, int KPT, bool TRANS>
+__global__ void __launch_bounds__(512) k_line_chain(ChainArgs<T> A) {
     if (A.skip && *A.skip) return;
     __shared__ T sh[64];
     const bool isY = blockIdx.x == 0;
     const Layout &lay = A.lay;
     const int L = lay.L;
-    const Region &C = lay.R[0], &X = lay.R[1], &Y = lay.R[2], &I = lay.R[3];
-    const Region &B = isY ? Y : X;
-    const int nlines = isY ? Y.mx : X.my;
+    const Region &B = isY ? lay.R[2] : lay.R[1];
+    const int nlines = isY ? lay.R[2].mx : lay.R[1].my;
     const int e0 = threadIdx.x * KPT;
     T zp[KPT], al[KPT], mu[KPT], y[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; q++) zp[q] = T(0);
+    LineData<T, KPT> cur, nxt;
+    if (nlines > 0) load_line<T, KPT, TRANS>(A, isY, nlines, 0, e0, cur);
     for (int li = 0; li < nlines; li++) {
+        if (li + 1 < nlines) load_line<T, KPT, TRANS>(A, isY, nlines, li + 1, e0, nxt);
         const int line = TRANS ? li : nlines - 1 - li;
         const long long base = B.off + (long long)line * L;
-        // right-hand side of this line
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
-            const int e = e0 + q;
-            if (e < L) {
-                const long long s = base + e;
-                T d = A.v[s];
-                if (!TRANS) {
-                    d -= (isY ? A.wE[s] : A.wN[s]) * zp[q];
-                    if (e == L - 1) {
-                        const long long pi = isY ? I.addr(line, 0) : I.addr(0, line);
-                        d -= (isY ? A.wN[s] : A.wE[s]) * A.z[pi];
-                    }
-                } else {
-                    T prev = zp[q];
-                    if (li == 0) prev = A.z[isY ? C.addr(L - 1, e) : C.addr(e, L - 1)];
-                    d -= (isY ? A.wET[s] : A.wNT[s]) * prev;
-                }
-                al[q] = d;
-                mu[q] = A.lf[s];
-            } else {
-                al[q] = T(0);
-                mu[q] = T(1);
-            }
+            const T prev = (TRANS && li == 0) ? cur.prev[q] : zp[q];
+            T d = cur.v[q] - cur.c[q] * prev;
+            if (!TRANS && e0 + q == L - 1) d -= cur.bval;
+            al[q] = d;
+            mu[q] = cur.f[q];
         }
         block_affine_scan<T, KPT, false>(al, mu, y, sh);
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
-            const int e = e0 + q;
-            if (e < L) {
-                const long long s = base + e;
-                al[q] = A.lg[s] * y[q];
-                mu[q] = A.lh[s];
-            } else {
-                al[q] = T(0);
-                mu[q] = T(1);
-            }
+            al[q] = cur.g[q] * y[q];
+            mu[q] = cur.h[q];
         }
         block_affine_scan<T, KPT, true>(al, mu, zp, sh);
 #pragma unroll
@@ -455,6 +468,7 @@ __global__ void __launch_bounds__(1024) k_line_chain(ChainArgs<T> A) {
             if (e < L) A.z[base + e] = zp[q];
             else zp[q] = T(0);
         }
+        cur = nxt;
     }
 }
 
@@ -468,12 +482,12 @@ static int launch_chains(blp_handle *h, const Coefs<T> &c, const T *v, T *z, con
     int L = h->L;
     // per line node: v, coupling, three factors, z = 6 words
     ProfScope ps(h, KC_LINE_CHAIN, (double)(h->lay.R[1].size + h->lay.R[2].size) * sizeof(T) * 6);
-    if (L <= 4096) {
+    if (L <= 2048) {
         int nt = ((L + 3) / 4 + 31) / 32 * 32;
         k_line_chain<T, 4, TRANS><<<2, nt, 0, h->stream>>>(a);
     } else {
-        int nt = ((L + 7) / 8 + 31) / 32 * 32;
-        k_line_chain<T, 8, TRANS><<<2, nt, 0, h->stream>>>(a);
+        int nt = ((L + 15) / 16 + 31) / 32 * 32;
+        k_line_chain<T, 16, TRANS><<<2, nt, 0, h->stream>>>(a);
     }
     LAUNCH_CHECK(h);
     return BLP_OK;
@@ -633,6 +647,268 @@ __global__ void k_corner_finish(double *partials, int nb, DevState *st, int mode
 }
 
 // ---------------------------------------------------------------------------
+// Fused coarse levels (Sec. 3.2 cycle below a size where a level fits in
+// shared memory).  One CTA runs the V(1,1) cycle from level l0 to the
+// coarsest and back: every level's iterate and right-hand side live in
+// shared memory (natural row-major layout), Gauss-Seidel is an in-place
+// anti-diagonal wavefront (the sequential downstream order exactly: a node
+// reads its E/N neighbours from the diagonal just updated and its W/S
+// neighbours still old), restriction and prolongation are CTA-parallel.
+// full = 1: l0 = 0 and the whole stationary iteration of M_CC (cycles and
+// the FE-scaled stopping test) runs here; full = 0: one cycle from a zero
+// iterate for the coarse-grid correction of level l0 - 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CoarseArgs {
+    int l0, nlev;                     // levels l0 .. nlev-1 are handled here
+    int m[BLP_MAXLEV];
+    const T *nat[BLP_MAXLEV];         // 10 natural arrays per level (see Level::nat)
+    const T *b_in;                    // right-hand side of level l0 (its SKEW layout)
+    T *e_out;                         // result on level l0 (SKEW layout)
+    Region R0;                        // level l0 SKEW region
+    int full, fixed_cycles, max_cycles;
+    double red2;                      // reduction factor squared
+    DevState *st;
+    const int *skip;
+};
+
+// Shared-memory image of one level inside the fused kernel (natural layout):
+// e, b, the four couplings of the sweep direction (forward wW, wE, wS, wN;
+// transpose wET, wWT, wNT, wST), omega = hb*kb*aC (restriction of the
+// forward cycle, prolongation of the transposed one) and the weight of the
+// stopping norm (forward omega, transpose hb*kb).
+template <typename T>
+struct CLev {
+    int m;
+    T *e, *b, *cw, *ce, *cs, *cn, *om, *wt;
+};
+
+// r = b - Op e at node (a, b) of a level (Op: normalised operator, or its transpose)
+template <typename T>
+__device__ __forceinline__ T coarse_residual(const CLev<T> L, int a, int bb) {
+    const int m = L.m, k = bb * m + a;
+    T s = L.e[k];
+    if (a > 0) s += L.cw[k] * L.e[k - 1];
+    if (a < m - 1) s += L.ce[k] * L.e[k + 1];
+    if (bb > 0) s += L.cs[k] * L.e[k - m];
+    if (bb < m - 1) s += L.cn[k] * L.e[k + m];
+    return L.b[k] - s;
+}
+
+// One downstream Gauss-Seidel sweep of a level, as an anti-diagonal wavefront
+// over shared memory; thread a owns column a (in-place: a node reads its E/N
+// neighbours from the diagonal just updated and its W/S neighbours still
+// old, which is the sequential order exactly).  Levels up to 32 wide run in
+// one warp.
+template <typename T, bool TRANS>
+__device__ __forceinline__ void coarse_gs_body(const CLev<T> L, int a, bool warp_only) {
+    const int m = L.m;
+    for (int step = 0; step < 2 * m - 1; step++) {
+        const int b = (TRANS ? step : 2 * m - 2 - step) - a;
+        if (a < m && b >= 0 && b < m) {
+            const int k = b * m + a;
+            T s = L.b[k];
+            if (a > 0) s -= L.cw[k] * L.e[k - 1];
+            if (a < m - 1) s -= L.ce[k] * L.e[k + 1];
+            if (b > 0) s -= L.cs[k] * L.e[k - m];
+            if (b < m - 1) s -= L.cn[k] * L.e[k + m];
+            L.e[k] = s;
+        }
+        if (warp_only) __syncwarp(); else __syncthreads();
+    }
+}
+
+template <typename T, bool TRANS>
+__device__ __forceinline__ void coarse_gs(const CLev<T> L) {
+    if (L.m <= 32) {
+        if (threadIdx.x < 32) coarse_gs_body<T, TRANS>(L, threadIdx.x, true);
+        __syncthreads();
+    } else {
+        coarse_gs_body<T, TRANS>(L, threadIdx.x, false);   // m <= blockDim.x
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T coarse_val(const T *ec, int mc, int I, int J) {
+    return (I < 1 || J < 1 || I > mc || J > mc) ? T(0) : ec[(J - 1) * mc + (I - 1)];
+}
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
+    if (A.skip && *A.skip) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[8];
+    CLev<T> LV[BLP_MAXLEV];
+    {
+        T *p = reinterpret_cast<T *>(smem_raw);
+        for (int l = A.l0; l < A.nlev; l++) {
+            const int m = A.m[l], n = m * m;
+            CLev<T> &L = LV[l];
+            L.m = m;
+            L.e = p; p += n;
+            L.b = p; p += n;
+            L.cw = p; p += n; L.ce = p; p += n; L.cs = p; p += n; L.cn = p; p += n; L.om = p; p += n;
+            L.wt = TRANS ? p : L.om;
+            if (TRANS) p += n;
+            const T *nat = A.nat[l];
+            const int q0 = TRANS ? 4 : 0;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                L.cw[k] = nat[(long long)(q0 + 0) * n + k];
+                L.ce[k] = nat[(long long)(q0 + 1) * n + k];
+                L.cs[k] = nat[(long long)(q0 + 2) * n + k];
+                L.cn[k] = nat[(long long)(q0 + 3) * n + k];
+                L.om[k] = nat[(long long)8 * n + k];
+                if (TRANS) L.wt[k] = nat[(long long)9 * n + k];
+            }
+        }
+    }
+    const int l0 = A.l0, last = A.nlev - 1, m0 = A.m[l0];
+    const Region R0 = A.R0;
+    for (int k = threadIdx.x; k < m0 * m0; k += blockDim.x) {
+        LV[l0].b[k] = A.b_in[R0.addr(k % m0, k / m0)];
+        LV[l0].e[k] = T(0);
+    }
+    __syncthreads();
+
+    auto vcycle = [&]() {
+        for (int l = l0; l < last; l++) {
+            const CLev<T> F = LV[l], Cc = LV[l + 1];
+            const int m = F.m, mc = Cc.m;
+            coarse_gs<T, TRANS>(F);
+            // restriction of the residual: forward b_c = omega_c^-1 P^T omega_f r, transpose b_c = P^T r
+            for (int q = threadIdx.x; q < mc * mc; q += blockDim.x) {
+                const int a0 = 2 * (q % mc) + 1, b0 = 2 * (q / mc) + 1;
+                T sum = T(0);
+                for (int db = -1; db <= 1; db++) {
+                    const int bb = b0 + db;
+                    if (bb < 0 || bb >= m) continue;
+                    for (int da = -1; da <= 1; da++) {
+                        const int a = a0 + da;
+                        if (a < 0 || a >= m) continue;
+                        T r = coarse_residual<T>(F, a, bb);
+                        if (!TRANS) r *= F.om[bb * m + a];
+                        sum += (da == 0 ? T(1) : T(0.5)) * (db == 0 ? T(1) : T(0.5)) * r;
+                    }
+                }
+                Cc.b[q] = TRANS ? sum : sum / Cc.om[q];
+                Cc.e[q] = T(0);
+            }
+            __syncthreads();
+        }
+        for (int s4 = 0; s4 < 4; s4++) coarse_gs<T, TRANS>(LV[last]);
+        for (int l = last - 1; l >= l0; l--) {
+            const CLev<T> F = LV[l], Cc = LV[l + 1];
+            const int m = F.m, mc = Cc.m;
+            for (int k = threadIdx.x; k < m * m; k += blockDim.x) {
+                const int I = k % m + 1, J = k / m + 1;
+                auto cv = [&](int Ic, int Jc) -> T {
+                    if (Ic < 1 || Jc < 1 || Ic > mc || Jc > mc) return T(0);
+                    const int kc = (Jc - 1) * mc + (Ic - 1);
+                    return TRANS ? Cc.e[kc] / Cc.om[kc] : Cc.e[kc];
+                };
+                T v;
+                const bool Ie = !(I & 1), Je = !(J & 1);
+                if (Ie && Je) v = cv(I / 2, J / 2);
+                else if (!Ie && Je) v = T(0.5) * (cv((I - 1) / 2, J / 2) + cv((I + 1) / 2, J / 2));
+                else if (Ie && !Je) v = T(0.5) * (cv(I / 2, (J - 1) / 2) + cv(I / 2, (J + 1) / 2));
+                else v = T(0.25) * (cv((I - 1) / 2, (J - 1) / 2) + cv((I + 1) / 2, (J - 1) / 2) +
+                                    cv((I - 1) / 2, (J + 1) / 2) + cv((I + 1) / 2, (J + 1) / 2));
+                if (TRANS) v *= F.om[k];
+                F.e[k] += v;
+            }
+            __syncthreads();
+            coarse_gs<T, TRANS>(F);
+        }
+    };
+
+    if (!A.full) {
+        vcycle();
+    } else {
+        // stationary iteration of M_CC with the stopping test on the FE-scaled residual
+        const CLev<T> L0 = LV[l0];
+        auto norm2 = [&](int resid) -> double {
+            const int n = m0 * m0;
+            double acc = 0.0;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                const T r = resid ? coarse_residual<T>(L0, k % m0, k / m0) : L0.b[k];
+                const double wr = (double)L0.wt[k] * (double)r;
+                acc += wr * wr;
+            }
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(FULL, acc, off);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+            __syncthreads();
+            return tot;
+        };
+        int cyc = 0;
+        if (A.fixed_cycles > 0) {
+            for (; cyc < A.fixed_cycles; cyc++) vcycle();
+        } else {
+            const double thresh = norm2(0) / A.red2;
+            if (thresh > 0.0) {
+                while (cyc < A.max_cycles) {
+                    vcycle();
+                    cyc++;
+                    if (norm2(1) <= thresh) break;
+                }
+            }
+        }
+        if (threadIdx.x == 0 && A.st) {
+            A.st->flags[1] = cyc;
+            A.st->flags[0] = 1;
+            atomicMax(&A.st->flags[3], cyc);
+        }
+    }
+    for (int k = threadIdx.x; k < m0 * m0; k += blockDim.x) A.e_out[R0.addr(k % m0, k / m0)] = LV[l0].e[k];
+}
+
+template <typename T>
+static size_t coarse_smem(const Hierarchy<T> &H, int l0) {
+    size_t b = 0;
+    for (int l = l0; l < H.nlev; l++) b += 8 * sizeof(T) * (size_t)H.lev[l].R.mx * H.lev[l].R.mx;
+    return b;
+}
+
+// first level handled by the fused coarse kernel (-1: none)
+template <typename T>
+static int coarse_start(const Hierarchy<T> &H) {
+    for (int l = 0; l < H.nlev; l++)
+        if (H.lev[l].nat && coarse_smem(H, l) <= 200 * 1024) return l;
+    return -1;
+}
+
+template <typename T, bool TRANS>
+static int launch_coarse(blp_handle *h, Hierarchy<T> &H, int l0, const T *b_in, T *e_out, int full, const int *skip) {
+    CoarseArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.l0 = l0; a.nlev = H.nlev;
+    for (int l = 0; l < H.nlev; l++) { a.m[l] = H.lev[l].R.mx; a.nat[l] = H.lev[l].nat; }
+    a.b_in = b_in; a.e_out = e_out; a.R0 = H.lev[l0].R;
+    a.full = full; a.fixed_cycles = h->p.corner_fixed_cycles; a.max_cycles = h->p.corner_max_cycles;
+    a.red2 = h->p.corner_reduction * h->p.corner_reduction;
+    a.st = h->dev; a.skip = skip;
+    const size_t smem = coarse_smem(H, l0);
+    static bool attr = false;
+    if (!attr) {
+        // dynamic bytes this kernel ever asks for (coarse_start caps them at 200 KB); it also
+        // has a little static shared memory, so the opt-in maximum itself would be rejected
+        if (cudaFuncSetAttribute(k_mg_coarse<T, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return BLP_ERR_CUDA;
+        }
+        attr = true;
+    }
+    double bytes = 0.0;
+    for (int l = l0; l < H.nlev; l++) bytes += 14.0 * sizeof(T) * H.lev[l].R.mx * H.lev[l].R.mx;
+    ProfScope ps(h, KC_MG_COARSE, bytes);
+    k_mg_coarse<T, TRANS><<<1, 256, smem, h->stream>>>(a);
+    LAUNCH_CHECK(h);
+    return BLP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
 template <typename T> static Coefs<T> &coefs_of(blp_handle *h);
@@ -650,6 +926,7 @@ struct Cycler {
     bool zero[BLP_MAXLEV];   // current iterate of the level is known to be 0
     const T *b0;             // level-0 right-hand side
     const int *skip;
+    int l0c;                 // first level of the fused coarse kernel (-1: none)
 
     int gs(int l, const T *b) {
         Level<T> &Lv = H->lev[l];
@@ -672,6 +949,11 @@ struct Cycler {
     int vcycle(int l) {
         Level<T> &Lv = H->lev[l];
         const T *b = l == 0 ? b0 : Lv.b;
+        if (l == l0c && l > 0) {   // coarse-grid correction from a zero iterate, fused
+            int rc = launch_coarse<T, TRANS>(h, *H, l, b, Lv.e[cur[l]], 0, skip);
+            zero[l] = false;
+            return rc;
+        }
         if (l == H->nlev - 1) {
             for (int s = 0; s < 4; s++) { int rc = gs(l, b); if (rc) return rc; }
             return BLP_OK;
@@ -704,8 +986,16 @@ struct Cycler {
 template <typename T, bool TRANS>
 static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out) {
     Hierarchy<T> &H = hier_of<T>(h);
+    const int l0c = coarse_start(H);
+    if (l0c == 0) {
+        // the whole corner iteration fits one CTA: a single launch, cycle count kept on the device
+        int rc = launch_coarse<T, TRANS>(h, H, 0, b0, H.lev[0].e[0], 1, nullptr);
+        *result = H.lev[0].e[0];
+        if (cycles_out) *cycles_out = -1;
+        return rc;
+    }
     Cycler<T, TRANS> cy;
-    cy.h = h; cy.H = &H; cy.b0 = b0;
+    cy.h = h; cy.H = &H; cy.b0 = b0; cy.l0c = l0c;
     for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
     cy.zero[0] = true;
     Level<T> &L0 = H.lev[0];

@@ -161,6 +161,17 @@ __global__ void k_pack_pairs(const double *__restrict__ a, const double *__restr
     }
 }
 
+// skew-layout level arrays -> natural row-major copies (10 arrays of m*m)
+struct NatSrc { const double *a[10]; };
+__global__ void k_to_natural(Region R, NatSrc src, double *nat) {
+    const int m = R.mx;
+    const int n = m * m;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long long p = R.addr(k % m, k / m);
+        for (int q = 0; q < 10; q++) nat[(long long)q * n + k] = src.a[q][p];
+    }
+}
+
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         b[k] = (float)a[k];
@@ -247,6 +258,7 @@ static void free_hier(Hierarchy<T> &H) {
         if (v.pF) cudaFree(v.pF);
         if (v.pR) cudaFree(v.pR);
         if (v.beta) cudaFree(v.beta);
+        if (v.nat) cudaFree(v.nat);
         T *ps[] = {v.wW, v.wE, v.wS, v.wN, v.wET, v.wNT, v.wWT, v.wST, v.omega, v.dfe, v.e[0], v.e[1], v.b};
         for (T *p : ps) if (p) cudaFree(p);
         v = Level<T>();
@@ -329,7 +341,8 @@ extern "C" int blp_kernel_class_count(void) { return KC_COUNT; }
 
 extern "C" const char *blp_kernel_class_name(int cls) {
     static const char *names[KC_COUNT] = {"dts_gs", "dts_interior", "line_chain", "mg_restrict", "mg_prolong",
-                                          "corner_norm", "matvec", "multidot", "update", "small", "layout", "gs_rhs"};
+                                          "corner_norm", "matvec", "multidot", "update", "small", "layout", "gs_rhs",
+                                          "mg_coarse"};
     return (cls >= 0 && cls < KC_COUNT) ? names[cls] : "";
 }
 
@@ -454,6 +467,16 @@ static int build_hierarchy(blp_handle *h) {
         TRY(dalloc(&F.beta, n));
         CUDA_TRY(cudaMemset(D.beta, 0, sizeof(double) * n));
         CUDA_TRY(cudaMemset(F.beta, 0, sizeof(float) * n));
+        if (ml <= BLP_COARSE_MAX) {
+            const long long nn = 10LL * ml * ml;
+            TRY(dalloc(&D.nat, nn));
+            TRY(dalloc(&F.nat, nn));
+            NatSrc src = {{D.wW, D.wE, D.wS, D.wN, D.wET, D.wWT, D.wNT, D.wST, D.omega, D.dfe}};
+            k_to_natural<<<grid_for((long long)ml * ml, 256), 256, 0, h->stream>>>(D.R, src, D.nat);
+            LAUNCH_CHECK(h);
+            k_to_float<<<grid_for(nn, 256), 256, 0, h->stream>>>(D.nat, F.nat, nn);
+            LAUNCH_CHECK(h);
+        }
         CUDA_TRY(cudaStreamSynchronize(h->stream));
     }
     cudaFree(dxs);
