@@ -131,6 +131,39 @@ int blp_apply_operator(blp_handle *h, const double *u, double *y, int transpose)
  * *cycles (may be NULL) receives the corner multigrid cycle count. */
 int blp_precond_apply(blp_handle *h, const double *v, double *z, int transpose, int precision, int *cycles);
 
+/* Largest N accepted by blp_residual_noalloc (its fixed scratch holds four
+ * partial sums per grid row: 4 * 8192 doubles = 256 KiB per device). */
+#define BLP_NOALLOC_MAX_N 8192
+
+/* Residual of the assembled operator without allocating anything and
+ * without a handle.  The paper has no counterpart: this is a library
+ * utility for callers that cannot allocate device memory when they check a
+ * solution -- device memory already fully reserved, a path where the
+ * device-wide synchronisation of cudaMalloc/cudaFree would stall other
+ * streams, or a monitor that holds no blp_handle.
+ *
+ * Computes s = f - A u, with A the upwind 5-point operator that blp_setup
+ * assembles for the tensor mesh x (N+1 nodes) by y (N+1 nodes), eps and the
+ * fields c1, c2, r, and writes
+ *     norms[0] = ||s||_2,        norms[1] = ||D^-1 s||_2,
+ *     norms[2] = ||f||_2,        norms[3] = ||D^-1 f||_2     (D = diag(A)).
+ * x, y, c1, c2, r, f, u: DEVICE (or managed) arrays, read only; fields have
+ * (N-1)^2 entries in the layout of the other calls.  res: device array of
+ * (N-1)^2 doubles receiving s, or NULL.  norms: 4 doubles, host or device,
+ * or NULL.  stream: a cudaStream_t (NULL: legacy default stream); the call
+ * returns after its work on that stream has completed.
+ * Errors: BLP_ERR_ARG for N odd, N < 8, N > BLP_NOALLOC_MAX_N, eps outside
+ * (0,1], or a null or host input array; BLP_ERR_CUDA when a CUDA call fails.
+ * Memory: reduction partials live in one fixed device array per device
+ * (BLP_NOALLOC_MAX_N bounds its size).  Its address is looked up on the
+ * first call on each device, so make that first call before any stream
+ * capture begins.  Every call on a device shares that array, so calls whose
+ * GPU work overlaps (different streams, or several host threads) race:
+ * serialise them. */
+int blp_residual_noalloc(int N, const double *x, const double *y, double eps, const double *c1,
+                         const double *c2, const double *r, const double *f, const double *u,
+                         double *res, double *norms, void *stream);
+
 /* Release the handle and all its device memory.  NULL is ignored. */
 void blp_destroy(blp_handle *h);
 

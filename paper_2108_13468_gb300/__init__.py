@@ -25,7 +25,7 @@ from ._native import (BLP_FP64, BLP_MIXED, BLP_STOP_ABS2, BLP_STOP_REL2, BLP_STO
                       Params)
 
 __all__ = ["mesh", "Solver", "Params", "Info", "BlpError", "BLP_FP64", "BLP_MIXED", "BLP_STOP_SCALED",
-           "BLP_STOP_REL2", "BLP_STOP_ABS2", "default_params", "solve"]
+           "BLP_STOP_REL2", "BLP_STOP_ABS2", "default_params", "solve", "residual_noalloc"]
 
 
 def default_params(**kw) -> Params:
@@ -152,6 +152,36 @@ class Solver:
 
     def kernel_launches(self):
         return self.lib.blp_kernel_launches(self.handle)
+
+
+def residual_noalloc(N, x, y, eps, c1, c2, r, f, u, res=None, stream=None):
+    """blp_residual_noalloc: residual f - A u and its norms, allocating no
+    device memory and needing no Solver.
+
+    For callers that cannot allocate device memory when they check a
+    solution (memory fully reserved, or a path where cudaMalloc's device-wide
+    synchronisation would stall other streams).  Every array must already be
+    on the device: x, y the N+1 mesh nodes, the fields (N-1)**2 values; res
+    (optional) receives f - A u.  Returns the host array
+    [||s||, ||D^-1 s||, ||f||, ||D^-1 f||] (s = f - A u, D = diag(A)).
+    N is limited to BLP_NOALLOC_MAX_N; calls on one device must not overlap.
+    """
+    if N > N_.BLP_NOALLOC_MAX_N:
+        raise ValueError(f"N={N} exceeds the no-allocation limit N <= {N_.BLP_NOALLOC_MAX_N}")
+    n = (N - 1) ** 2
+    ptrs = [_ptr(a, N + 1)[0] for a in (x, y)] + [_ptr(a, n)[0] for a in (c1, c2, r, f, u)]
+    rp = _ptr(res, n, True)[0] if res is not None else None
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    norms = np.zeros(4)
+    st = N_.load().blp_residual_noalloc(N, ptrs[0], ptrs[1], float(eps), *ptrs[2:], rp,
+                                        ctypes.c_void_p(norms.ctypes.data), ctypes.c_void_p(stream))
+    if st == N_.BLP_ERR_ARG:
+        raise BlpError(st, f"blp_residual_noalloc (N={N}: even, 8 <= N <= {N_.BLP_NOALLOC_MAX_N}; "
+                           "0 < eps <= 1; every input on the device)")
+    N_.check(st, "blp_residual_noalloc")
+    return norms
 
 
 def solve(f, c1, c2, r, N, eps, tol=1e-10, **params):

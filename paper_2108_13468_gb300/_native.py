@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libblp.so")
 BLP_OK, BLP_ERR_ARG, BLP_ERR_COEF, BLP_ERR_NOCONV, BLP_ERR_TIMEOUT, BLP_ERR_CUDA, BLP_ERR_MEM = range(7)
 BLP_FP64, BLP_MIXED = 0, 1
 BLP_STOP_SCALED, BLP_STOP_REL2, BLP_STOP_ABS2 = 0, 1, 2
+BLP_NOALLOC_MAX_N = 8192
 
 c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -53,6 +54,8 @@ SIGNATURES = {
     "blp_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(c_ll), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "blp_kernel_class_count": (c_int, []),
     "blp_kernel_class_name": (ctypes.c_char_p, [c_int]),
+    "blp_residual_noalloc": (c_int, [c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     # host-side layout inspection (no GPU needed)
     "blp_layout_npad": (c_ll, [c_int]),
     "blp_layout_addr": (c_ll, [c_int, c_int, c_int]),
