@@ -404,14 +404,19 @@ def run_profile_target(args):
     prec = blp.BLP_MIXED if args.precision == "mixed" else blp.BLP_FP64
     c1, c2, r, f = [torch.from_numpy(a).to(dev) for a in build_inputs(N, [eps])[eps]]
     s = blp.Solver(N, eps, c1, c2, r, precision=prec)
+    lib = s.lib
     if args.mode == "precond":
         v = torch.from_numpy(np.random.default_rng(0).standard_normal((N - 1) ** 2)).to(dev)
-        for _ in range(2):
-            s.precond(v, precision=prec)
+        s.precond(v, precision=prec)
+        lib.blp_profile(s.handle, 1)     # event-time the second application
+        s.precond(v, precision=prec)
     else:
+        lib.blp_profile(s.handle, 1)
         s.solve(f, tol=TOL)
     torch.cuda.synchronize()
+    classes = merge_profiles([read_profile(lib, s)])
     print(f"profile target done: mode={args.mode} N={N} eps={eps:g} precision={args.precision}")
+    print(json.dumps({"kernel_classes": classes}))
 
 
 if __name__ == "__main__":

@@ -231,6 +231,8 @@ struct blp_handle {
     int *err = nullptr;             // device error word (timeouts)
     cudaStream_t stream = 0;
     long long launches = 0;
+    int dts_max_cluster = 8;        // CTAs per wavefront cluster (1..8)
+    int dts_chunk = 16;             // wavefront chunk length (8 or 16 diagonals)
     double t_setup_ms = 0.0;
     int last_cycles = 0;
     // Krylov work space (allocated lazily)

@@ -2,6 +2,7 @@
 // factorisations, corner multigrid hierarchy, layout conversion and the
 // handle life cycle.
 #include "blp_common.cuh"
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <chrono>
@@ -570,6 +571,9 @@ extern "C" int blp_setup(const blp_params *p, const double *c1, const double *c2
     auto t0 = std::chrono::steady_clock::now();
     blp_handle *h = new blp_handle();
     h->p = *p;
+    // tuning override: CTAs per wavefront cluster (1 = single-SM wavefront)
+    if (const char *e = getenv("BLP_DTS_CLUSTER")) h->dts_max_cluster = std::max(1, std::min(8, atoi(e)));
+    if (const char *e = getenv("BLP_DTS_CHUNK")) h->dts_chunk = atoi(e) == 8 ? 8 : 16;
     h->stream = 0;
     int rc = setup_impl(h, c1, c2, r);
     if (rc != BLP_OK) {
