@@ -8,6 +8,7 @@
 #include "blp_common.cuh"
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
 
@@ -653,6 +654,152 @@ __global__ void __launch_bounds__(512) k_line_chain(ChainArgs<T> A) {
     }
 }
 
+// Line chains for L <= 2048 with 16-byte aligned lines (L * sizeof(T) a
+// multiple of 16): the line data (right-hand side, coupling, three factors,
+// boundary term) stream into NS shared-memory stages with 16-byte cp.async,
+// NS-1 lines ahead of the solve.  Thread t owns the KPT consecutive nodes
+// [t*KPT, t*KPT+KPT) of a line; each such segment is followed by 16 bytes
+// of padding, so the 16-byte vector reads of a warp hit distinct banks.
+// NW = 1 keeps both scans inside one warp (no CTA barrier).
+template <typename T, int KPT, int NW>
+struct ChainSmem {
+    static constexpr int VEC = 16 / sizeof(T);         // elements per 16 bytes
+    static constexpr int LP = 32 * NW * KPT;           // padded line length
+    static constexpr int LPP = LP / KPT * (KPT + VEC);  // with 16 bytes after each segment
+    static constexpr size_t stage_elems = (size_t)5 * LPP + VEC;
+    static constexpr size_t stage = stage_elems * sizeof(T);
+    static __device__ __forceinline__ int at(int e) { return e / KPT * (KPT + VEC) + e % KPT; }
+};
+
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_word(T *dst, const T *src) {
+    if constexpr (sizeof(T) == 4) cp_async_4(dst, src); else cp_async_8(dst, src);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T, int KPT, int NW, int NS, bool TRANS>
+__global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
+    typedef ChainSmem<T, KPT, NW> SM;
+    constexpr int VEC = SM::VEC, NV = KPT / VEC;
+    typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
+    if (A.skip && *A.skip) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *const stg = reinterpret_cast<T *>(smem_raw);
+    __shared__ T sh[64];
+    const bool isY = blockIdx.x == 0;
+    const Layout &lay = A.lay;
+    const int L = lay.L;
+    const Region &B = isY ? lay.R[2] : lay.R[1];
+    const Region &C = lay.R[0], &I = lay.R[3];
+    const int nlines = isY ? lay.R[2].mx : lay.R[1].my;
+    const int tid = threadIdx.x, nthr = 32 * NW;
+    const int e0 = tid * KPT;
+    const T *const cpl = TRANS ? (isY ? A.wET : A.wNT) : (isY ? A.wE : A.wN);
+    const T *const bcpl = isY ? A.wN : A.wE;
+    const int nvec = L / VEC;
+
+    // line li's data into stage li % NS (one commit group per line)
+    auto issue = [&](int li) {
+        if (li < nlines) {
+            const int line = TRANS ? li : nlines - 1 - li;
+            const long long base = B.off + (long long)line * L;
+            T *st = stg + (size_t)(li % NS) * SM::stage_elems;
+            for (int k = tid; k < nvec; k += nthr) {
+                const int e = k * VEC, p = SM::at(e);
+                cp_async_16(st + p, A.v + base + e);
+                cp_async_16(st + SM::LPP + p, cpl + base + e);
+                cp_async_16(st + 2 * SM::LPP + p, A.lf + base + e);
+                cp_async_16(st + 3 * SM::LPP + p, A.lg + base + e);
+                cp_async_16(st + 4 * SM::LPP + p, A.lh + base + e);
+            }
+            if (!TRANS && tid == nthr - 1) {   // boundary term of the last node: coupling * z_I
+                const long long pi = isY ? I.addr(line, 0) : I.addr(0, line);
+                cp_async_word(st + 5 * SM::LPP, bcpl + base + (L - 1));
+                cp_async_word(st + 5 * SM::LPP + 1, A.z + pi);
+            }
+        }
+        cp_async_commit();
+    };
+
+    T zp[KPT], al[KPT], mu[KPT], y[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; q++) {   // transposed chain: the first line couples to C
+        const int e = e0 + q;
+        zp[q] = (TRANS && e < L && nlines > 0) ? A.z[isY ? C.addr(L - 1, e) : C.addr(e, L - 1)] : T(0);
+    }
+    for (int li = 0; li < NS - 1; li++) issue(li);
+    for (int li = 0; li < nlines; li++) {
+        issue(li + NS - 1);          // the stage of line li-1, read completely by now
+        cp_async_wait<NS - 1>();     // this thread's copies of line li have landed
+        if (NW == 1) __syncwarp(); else __syncthreads();
+        const T *st = stg + (size_t)(li % NS) * SM::stage_elems;
+        const int line = TRANS ? li : nlines - 1 - li;
+        const long long base = B.off + (long long)line * L;
+        T vv[KPT], cc[KPT], ff[KPT], g[KPT], hh[KPT];
+        const int p0 = tid * (KPT + VEC);
+#pragma unroll
+        for (int r = 0; r < NV; r++) {
+            const int p = p0 + r * VEC;
+            *reinterpret_cast<V *>(vv + r * VEC) = *reinterpret_cast<const V *>(st + p);
+            *reinterpret_cast<V *>(cc + r * VEC) = *reinterpret_cast<const V *>(st + SM::LPP + p);
+            *reinterpret_cast<V *>(ff + r * VEC) = *reinterpret_cast<const V *>(st + 2 * SM::LPP + p);
+            *reinterpret_cast<V *>(g + r * VEC) = *reinterpret_cast<const V *>(st + 3 * SM::LPP + p);
+            *reinterpret_cast<V *>(hh + r * VEC) = *reinterpret_cast<const V *>(st + 4 * SM::LPP + p);
+        }
+        T bval = T(0);
+        if (!TRANS && e0 <= L - 1 && L - 1 < e0 + KPT) bval = st[5 * SM::LPP] * st[5 * SM::LPP + 1];
+#pragma unroll
+        for (int q = 0; q < KPT; q++) {
+            const int e = e0 + q;
+            if (e < L) {
+                T d = vv[q] - cc[q] * zp[q];
+                if (!TRANS && e == L - 1) d -= bval;
+                al[q] = d;
+                mu[q] = ff[q];
+            } else {
+                al[q] = T(0); mu[q] = T(1); g[q] = T(0); hh[q] = T(1);
+            }
+        }
+        block_affine_scan<T, KPT, false>(al, mu, y, sh);
+#pragma unroll
+        for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
+        block_affine_scan<T, KPT, true>(al, mu, zp, sh);
+#pragma unroll
+        for (int r = 0; r < NV; r++)
+            if (e0 + r * VEC < L) *reinterpret_cast<V *>(A.z + base + e0 + r * VEC) = *reinterpret_cast<const V *>(zp + r * VEC);
+    }
+    cp_async_wait<0>();
+}
+
+template <typename T, int KPT, int NW, int NS, bool TRANS>
+static int launch_chain2(blp_handle *h, const ChainArgs<T> &a) {
+    constexpr size_t smem = NS * ChainSmem<T, KPT, NW>::stage;
+    static_assert(smem <= 200 * 1024, "line-chain stages exceed the shared-memory budget");
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(k_line_chain2<T, KPT, NW, NS, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return BLP_ERR_CUDA;
+        }
+        attr_set = true;
+    }
+    k_line_chain2<T, KPT, NW, NS, TRANS><<<2, 32 * NW, smem, h->stream>>>(a);
+    LAUNCH_CHECK(h);
+    return BLP_OK;
+}
+
 template <typename T, bool TRANS>
 static int launch_chains(blp_handle *h, const Coefs<T> &c, const T *v, T *z, const int *skip) {
     ChainArgs<T> a;
@@ -663,7 +810,21 @@ static int launch_chains(blp_handle *h, const Coefs<T> &c, const T *v, T *z, con
     int L = h->L;
     // per line node: v, coupling, three factors, z = 6 words
     ProfScope ps(h, KC_LINE_CHAIN, (double)(h->lay.R[1].size + h->lay.R[2].size) * sizeof(T) * 6);
-    if (L <= 2048) {
+    const bool aligned16 = (L * sizeof(T)) % 16 == 0 && (h->lay.R[1].off * sizeof(T)) % 16 == 0 &&
+                           (h->lay.R[2].off * sizeof(T)) % 16 == 0;
+    if (L <= 2048 && aligned16) {
+        // FP32: short FMA latency, so one warp per chain (longer thread
+        // segments, no CTA barrier); FP64: 4 warps to cut the sequential part
+        if constexpr (sizeof(T) == 4) {
+            if (L <= 512) return launch_chain2<T, 16, 1, 8, TRANS>(h, a);
+            if (L <= 1024) return launch_chain2<T, 16, 2, 6, TRANS>(h, a);
+            return launch_chain2<T, 16, 4, 3, TRANS>(h, a);
+        } else {
+            if (L <= 512) return launch_chain2<T, 4, 4, 6, TRANS>(h, a);
+            if (L <= 1024) return launch_chain2<T, 8, 4, 3, TRANS>(h, a);
+            return launch_chain2<T, 16, 4, 2, TRANS>(h, a);
+        }
+    } else if (L <= 2048) {
         int nt = ((L + 3) / 4 + 31) / 32 * 32;
         k_line_chain<T, 4, TRANS><<<2, nt, 0, h->stream>>>(a);
     } else {
