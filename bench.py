@@ -193,14 +193,9 @@ def run_ours(args):
             d["ms"].append(ms)
     barrier()
     clocks = sampler.stop()
-    step_ms = total_ms / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(total_ms / args.steps, dev)
     units = n * len(eps_list) * len(precisions)
-    value = units * world / (step_ms * 1e-3)
+    value = whole_job_value(units, world, step_ms)
 
     # e2e: host (pinned) inputs, host output, through the public API
     e2e = None
@@ -259,6 +254,23 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def max_over_ranks(step_ms, dev=None):
+    """Replicas: the job's step time is the slowest rank's (max over ranks);
+    a single process returns its own time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return step_ms
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, step_ms):
+    """Unknowns solved by all ranks per second of the (max-over-ranks) step."""
+    return units_per_rank * world / (step_ms * 1e-3)
 
 
 def read_profile(lib, s):

@@ -131,6 +131,29 @@ int blp_apply_operator(blp_handle *h, const double *u, double *y, int transpose)
  * *cycles (may be NULL) receives the corner multigrid cycle count. */
 int blp_precond_apply(blp_handle *h, const double *v, double *z, int transpose, int precision, int *cycles);
 
+/* One problem of a batch: its parameters, fields, right-hand side, initial
+ * guess / solution, tolerance, and (on return) its statistics and status. */
+typedef struct {
+    blp_params params;             /* N, eps, precision, ... of this problem */
+    const double *c1, *c2, *r;     /* (N-1)^2 fields, host or device */
+    const double *f;               /* right-hand side */
+    double *u;                     /* initial guess on entry, solution on exit */
+    double tol;                    /* tolerance for params.stop_mode */
+    blp_info info;                 /* out: statistics of this solve */
+    int status;                    /* out: BLP_OK or the error of this problem */
+} blp_batch_item;
+
+/* Solve `count` independent problems (Sec. 3.3 solve of each; the batched
+ * workload of many small problems with different N and eps).  Up to
+ * `concurrency` problems (<= 0: 8) are in flight at once, each on its own
+ * stream of the current device, set up, solved and released by one of
+ * `concurrency` host threads.  Per-problem conventions are those of
+ * blp_setup + blp_solve; items[i].status and items[i].info report each
+ * problem.  Returns BLP_OK when every problem succeeded, else the status of
+ * the first (lowest-index) failed problem; BLP_ERR_ARG for count < 0 or a
+ * null array.  The caller's arrays must stay valid until the call returns. */
+int blp_solve_batched(blp_batch_item *items, int count, int concurrency);
+
 /* Largest N accepted by blp_residual_noalloc (its fixed scratch holds four
  * partial sums per grid row: 4 * 8192 doubles = 256 KiB per device). */
 #define BLP_NOALLOC_MAX_N 8192
@@ -163,6 +186,16 @@ int blp_precond_apply(blp_handle *h, const double *v, double *z, int transpose, 
 int blp_residual_noalloc(int N, const double *x, const double *y, double eps, const double *c1,
                          const double *c2, const double *r, const double *f, const double *u,
                          double *res, double *norms, void *stream);
+
+/* Self-check of the device-side bounded waits (no counterpart in the
+ * paper): one warp waits, with the same helpers the wavefront kernel uses
+ * and a short iteration limit, for a shared-memory counter and an mbarrier
+ * phase that nothing completes.  Both waits must give up and record a
+ * timeout; the call returns BLP_ERR_TIMEOUT when they did (the expected
+ * result), BLP_OK if either wait did not report, BLP_ERR_CUDA on a CUDA
+ * failure.  The handle's error word is cleared afterwards, so the handle
+ * stays usable. */
+int blp_check_wait_timeout(blp_handle *h);
 
 /* Release the handle and all its device memory.  NULL is ignored. */
 void blp_destroy(blp_handle *h);

@@ -25,7 +25,7 @@ from ._native import (BLP_FP64, BLP_MIXED, BLP_STOP_ABS2, BLP_STOP_REL2, BLP_STO
                       Params)
 
 __all__ = ["mesh", "Solver", "Params", "Info", "BlpError", "BLP_FP64", "BLP_MIXED", "BLP_STOP_SCALED",
-           "BLP_STOP_REL2", "BLP_STOP_ABS2", "default_params", "solve", "residual_noalloc"]
+           "BLP_STOP_REL2", "BLP_STOP_ABS2", "default_params", "solve", "solve_batched", "residual_noalloc"]
 
 
 def default_params(**kw) -> Params:
@@ -152,6 +152,45 @@ class Solver:
 
     def kernel_launches(self):
         return self.lib.blp_kernel_launches(self.handle)
+
+
+def solve_batched(problems, tol=1e-10, concurrency=8):
+    """blp_solve_batched: independent problems solved concurrently.
+
+    problems: list of dicts with keys N, eps, c1, c2, r, f (float64 arrays or
+    tensors of (N-1)**2 values, host or device), optional u (initial guess,
+    overwritten with the solution) and any blp_params field.  Returns a list
+    of (u, Info); raises BlpError if any problem failed (the per-problem
+    statuses are in the Info objects of the exception's .results)."""
+    lib = N_.load()
+    n = len(problems)
+    items = (N_.BatchItem * n)()
+    keep, outs = [], []
+    for k, pr in enumerate(problems):
+        pr = dict(pr)
+        N, eps = pr.pop("N"), pr.pop("eps")
+        nn = (N - 1) ** 2
+        fields = [pr.pop(key) for key in ("c1", "c2", "r", "f")]
+        u = pr.pop("u", None)
+        if u is None:
+            try:
+                import torch
+                u = torch.zeros_like(fields[3]) if isinstance(fields[3], torch.Tensor) else np.zeros(nn)
+            except ImportError:
+                u = np.zeros(nn)
+        items[k].params = default_params(N=N, eps=eps, **pr)
+        ptrs = [_ptr(a, nn) for a in fields] + [_ptr(u, nn, True)]
+        keep.append(ptrs)
+        items[k].c1, items[k].c2, items[k].r, items[k].f, items[k].u = [q[0] for q in ptrs]
+        items[k].tol = tol
+        outs.append(u)
+    st = lib.blp_solve_batched(items, n, int(concurrency))
+    results = [(outs[k], items[k].info) for k in range(n)]
+    if st != N_.BLP_OK:
+        err = BlpError(st, "blp_solve_batched")
+        err.results = results
+        raise err
+    return results
 
 
 def residual_noalloc(N, x, y, eps, c1, c2, r, f, u, res=None, stream=None):

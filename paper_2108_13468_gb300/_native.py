@@ -36,6 +36,11 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("params", Params), ("c1", c_void_p), ("c2", c_void_p), ("r", c_void_p), ("f", c_void_p),
+                ("u", c_void_p), ("tol", c_double), ("info", Info), ("status", c_int)]
+
+
 # exported symbol -> (restype, argtypes); the ABI test checks this against include/blp.h
 SIGNATURES = {
     "blp_params_default": (None, [ctypes.POINTER(Params)]),
@@ -54,6 +59,8 @@ SIGNATURES = {
     "blp_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(c_ll), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "blp_kernel_class_count": (c_int, []),
     "blp_kernel_class_name": (ctypes.c_char_p, [c_int]),
+    "blp_check_wait_timeout": (c_int, [c_void_p]),
+    "blp_solve_batched": (c_int, [ctypes.POINTER(BatchItem), c_int, c_int]),
     "blp_residual_noalloc": (c_int, [c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     # host-side layout inspection (no GPU needed)

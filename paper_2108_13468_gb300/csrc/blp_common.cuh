@@ -243,6 +243,13 @@ struct blp_handle {
     ProfState prof;
 };
 
+// Stream-ordered device allocation from the library pool (handle's stream).
+int blp_internal_alloc(blp_handle *h, void **p, size_t bytes);
+void blp_internal_free(blp_handle *h, void *p);
+// blp_setup with the handle's work issued on `stream` from the start.
+int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, const double *r, cudaStream_t stream,
+                       blp_handle **out);
+
 // Event timing of one launch when profiling is on (RAII around a launch).
 int blp_internal_prof_flush(blp_handle *h);
 struct ProfScope {

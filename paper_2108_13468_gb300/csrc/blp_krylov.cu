@@ -493,7 +493,8 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     if (e) status = e;
     {
         int devmax = 0;
-        CUDA_TRY(cudaMemcpy(&devmax, &h->dev->flags[3], sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpyAsync(&devmax, &h->dev->flags[3], sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
         if (devmax > maxcyc) maxcyc = devmax;
     }
     if (info) {
@@ -605,7 +606,8 @@ extern "C" int blp_precond_apply(blp_handle *h, const double *v, double *z, int 
     }
     if (cyc < 0) {   // counted on the device by the fused corner kernel
         CUDA_TRY(cudaStreamSynchronize(h->stream));
-        CUDA_TRY(cudaMemcpy(&cyc, &h->dev->flags[1], sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpyAsync(&cyc, &h->dev->flags[1], sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
     }
     bool zdev = is_dev(z);
     double *zd = zdev ? z : h->stage[2];

@@ -7,6 +7,7 @@
 //                      smoother + fused restriction / prolongation kernels
 #include "blp_common.cuh"
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <type_traits>
 #include <cooperative_groups.h>
@@ -172,12 +173,12 @@ __device__ __forceinline__ bool mbar_test_wait_cluster(unsigned long long *bar, 
     return ok != 0;
 }
 __device__ __forceinline__ void mbar_wait_cluster(unsigned long long *bar, unsigned parity, volatile unsigned *abort_flag,
-                                                  int *err) {
+                                                  int *err, long long limit = BLP_SPIN_LIMIT >> 4) {
     if (mbar_test_wait_cluster(bar, parity)) return;   // usually complete already
     long long n = 0;
     while (!mbar_try_wait_cluster(bar, parity)) {
         if (*abort_flag) return;
-        if (++n > (BLP_SPIN_LIMIT >> 4)) {
+        if (++n > limit) {
             *abort_flag = 1u;
             atomicExch(err, BLP_ERR_TIMEOUT);
             return;
@@ -185,11 +186,12 @@ __device__ __forceinline__ void mbar_wait_cluster(unsigned long long *bar, unsig
     }
 }
 // bounded wait until the local counter *ctr (written by a peer) >= target
-__device__ __forceinline__ void wait_counter(const unsigned *ctr, int target, volatile unsigned *abort_flag, int *err) {
+__device__ __forceinline__ void wait_counter(const unsigned *ctr, int target, volatile unsigned *abort_flag, int *err,
+                                             long long limit = BLP_SPIN_LIMIT) {
     long long n = 0;
     while ((int)ld_acquire_cluster(ctr) < target) {
         if (*abort_flag) return;
-        if (++n > BLP_SPIN_LIMIT) {
+        if (++n > limit) {
             *abort_flag = 1u;
             atomicExch(err, BLP_ERR_TIMEOUT);
             return;
@@ -420,6 +422,40 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
     cluster.sync();
 }
 
+// Self-check of the bounded waits: one warp waits, with the kernels' own
+// helpers and a short iteration limit, for a counter and an mbarrier phase
+// that nothing completes.  Each wait must give up, record BLP_ERR_TIMEOUT
+// and return; err[0] / err[1] receive the two outcomes.
+__global__ void k_wait_probe(int *err, long long limit) {
+    __shared__ unsigned ctr;
+    __shared__ unsigned abort_flag;
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        ctr = 0u;
+        abort_flag = 0u;
+        mbar_init(&bar, 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncthreads();
+    wait_counter(&ctr, 1, &abort_flag, err, limit);
+    __syncwarp();
+    if (threadIdx.x == 0) abort_flag = 0u;
+    __syncwarp();
+    mbar_wait_cluster(&bar, 0u, &abort_flag, err + 1, limit);
+}
+
+extern "C" int blp_check_wait_timeout(blp_handle *h) {
+    if (!h) return BLP_ERR_ARG;
+    int res[2] = {0, 0};
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+    k_wait_probe<<<1, 32, 0, h->stream>>>(h->err, 2000);
+    LAUNCH_CHECK(h);
+    CUDA_TRY(cudaMemcpyAsync(res, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return (res[0] == BLP_ERR_TIMEOUT && res[1] == BLP_ERR_TIMEOUT) ? BLP_ERR_TIMEOUT : BLP_OK;
+}
+
 // Cluster shape for a block of S strips: CL <= max_cluster CTAs (one per
 // SM: the dynamic shared memory is padded so that two CTAs cannot share an
 // SM) of WC <= 15 compute warps, and as many bulk-copy stages as fit.
@@ -443,7 +479,7 @@ static DtsShape dts_shape(int S, int max_cluster) {
 
 template <typename T, bool REV, int CH>
 static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls) {
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};
     if (!attr_set) {
         if (cudaFuncSetAttribute(k_dts<T, REV, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess ||
             cudaFuncSetAttribute(k_dts<T, REV, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess) {
@@ -786,7 +822,7 @@ template <typename T, int KPT, int NW, int NS, bool TRANS>
 static int launch_chain2(blp_handle *h, const ChainArgs<T> &a) {
     constexpr size_t smem = NS * ChainSmem<T, KPT, NW>::stage;
     static_assert(smem <= 200 * 1024, "line-chain stages exceed the shared-memory budget");
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};
     if (!attr_set) {
         if (cudaFuncSetAttribute(k_line_chain2<T, KPT, NW, NS, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024) != cudaSuccess) {
@@ -1232,7 +1268,7 @@ static int launch_coarse(blp_handle *h, Hierarchy<T> &H, int l0, const T *b_in, 
     a.red2 = h->p.corner_reduction * h->p.corner_reduction;
     a.st = h->dev; a.skip = skip;
     const size_t smem = coarse_smem(H, l0);
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         // dynamic bytes this kernel ever asks for (coarse_start caps them at 200 KB); it also
         // has a little static shared memory, so the opt-in maximum itself would be rejected

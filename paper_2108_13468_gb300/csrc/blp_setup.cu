@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <chrono>
+#include <mutex>
 
 // ---------------------------------------------------------------------------
 // S0. Shishkin mesh (Sec. 2.2 eq. (tau 1D); Sec. 3 eq. (tau exponential)).
@@ -232,9 +233,44 @@ __global__ void k_check_coefs(const double *c1, const double *c2, const double *
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-template <typename T>
-static int dalloc(T **p, long long n) {
-    if (cudaMalloc((void **)p, sizeof(T) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
+// Device memory of a handle comes from one library-owned stream-ordered
+// pool per device: allocations and frees are ordered on the handle's
+// stream and never synchronise the device, so handles on different streams
+// (the batched solver) run concurrently; up to 4 GiB of freed memory stays
+// in the pool for reuse.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static int lib_pool(cudaMemPool_t *out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return BLP_ERR_CUDA; }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { cudaGetLastError(); return BLP_ERR_CUDA; }
+        unsigned long long keep = 4ULL << 30;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            cudaMemPoolDestroy(pool);
+            return BLP_ERR_CUDA;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return BLP_OK;
+}
+
+int blp_internal_alloc(blp_handle *h, void **p, size_t bytes) {
+    cudaMemPool_t pool;
+    *p = nullptr;
+    int rc = lib_pool(&pool);
+    if (rc != BLP_OK) return rc;
+    if (cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, h->stream) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return BLP_ERR_MEM;
@@ -242,26 +278,62 @@ static int dalloc(T **p, long long n) {
     return BLP_OK;
 }
 
+void blp_internal_free(blp_handle *h, void *p) {
+    if (p && cudaFreeAsync(p, h->stream) != cudaSuccess) cudaGetLastError();
+}
+
+// Page-locked host mirrors of DevState, recycled across handles (page-locked
+// allocation would synchronise the device).
+static std::mutex g_pinned_mu;
+static std::vector<DevState *> g_pinned_free;
+
+static DevState *pinned_get() {
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            DevState *d = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return d;
+        }
+    }
+    DevState *d = nullptr;
+    if (cudaMallocHost((void **)&d, sizeof(DevState)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return d;
+}
+static void pinned_put(DevState *d) {
+    if (!d) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.push_back(d);
+}
+
+template <typename T>
+static int dalloc(blp_handle *h, T **p, long long n) {
+    void *q = nullptr;
+    int rc = blp_internal_alloc(h, &q, sizeof(T) * (size_t)(n > 0 ? n : 1));
+    *p = static_cast<T *>(q);
+    return rc;
+}
+
 #define TRY(x) do { int rc_ = (x); if (rc_ != BLP_OK) return rc_; } while (0)
 
 template <typename T>
-static void free_coefs(Coefs<T> &c) {
-    if (c.pF) cudaFree(c.pF);
-    if (c.pR) cudaFree(c.pR);
+static void free_coefs(blp_handle *h, Coefs<T> &c) {
+    blp_internal_free(h, c.pF);
+    blp_internal_free(h, c.pR);
     T *ps[] = {c.wW, c.wE, c.wS, c.wN, c.wET, c.wNT, c.wWT, c.wST, c.lf, c.lg, c.lh, c.lfT, c.lgT, c.lhT};
-    for (T *p : ps) if (p) cudaFree(p);
+    for (T *p : ps) blp_internal_free(h, p);
     c = Coefs<T>();
 }
 template <typename T>
-static void free_hier(Hierarchy<T> &H) {
+static void free_hier(blp_handle *h, Hierarchy<T> &H) {
     for (int l = 0; l < H.nlev; l++) {
         Level<T> &v = H.lev[l];
-        if (v.pF) cudaFree(v.pF);
-        if (v.pR) cudaFree(v.pR);
-        if (v.beta) cudaFree(v.beta);
-        if (v.nat) cudaFree(v.nat);
+        blp_internal_free(h, v.pF);
+        blp_internal_free(h, v.pR);
+        blp_internal_free(h, v.beta);
+        blp_internal_free(h, v.nat);
         T *ps[] = {v.wW, v.wE, v.wS, v.wN, v.wET, v.wNT, v.wWT, v.wST, v.omega, v.dfe, v.e[0], v.e[1], v.b};
-        for (T *p : ps) if (p) cudaFree(p);
+        for (T *p : ps) blp_internal_free(h, p);
         v = Level<T>();
     }
     H.nlev = 0;
@@ -270,16 +342,17 @@ static void free_hier(Hierarchy<T> &H) {
 extern "C" void blp_destroy(blp_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    free_coefs(h->cd);
-    free_coefs(h->cf);
-    free_hier(h->hd);
-    free_hier(h->hf);
+    free_coefs(h, h->cd);
+    free_coefs(h, h->cf);
+    free_hier(h, h->hd);
+    free_hier(h, h->hf);
     blp_internal_prof_flush(h);
     for (auto &e : h->prof.ev) cudaEventDestroy(e);
     void *ps[] = {h->x, h->y, h->aC, h->c1, h->c2, h->r, h->partials, h->dev, h->err, h->ws,
                   h->stage[0], h->stage[1], h->stage[2], h->stage[3]};
-    for (void *p : ps) if (p) cudaFree(p);
-    if (h->host_state) cudaFreeHost(h->host_state);
+    for (void *p : ps) blp_internal_free(h, p);
+    pinned_put(h->host_state);
+    cudaStreamSynchronize(h->stream);
     delete h;
 }
 
@@ -349,8 +422,9 @@ extern "C" const char *blp_kernel_class_name(int cls) {
 
 int blp_internal_ensure_ws(blp_handle *h, size_t bytes) {
     if (h->ws_bytes >= bytes) return BLP_OK;
-    if (h->ws) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0; }
-    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return BLP_ERR_MEM; }
+    if (h->ws) { blp_internal_free(h, h->ws); h->ws = nullptr; h->ws_bytes = 0; }
+    int rc = blp_internal_alloc(h, &h->ws, bytes);
+    if (rc != BLP_OK) return rc;
     h->ws_bytes = bytes;
     return BLP_OK;
 }
@@ -370,11 +444,11 @@ int blp_internal_from_region(blp_handle *h, const double *in, double *out, int s
 }
 
 template <typename T>
-static int alloc_coefs(Coefs<T> &c, long long n) {
+static int alloc_coefs(blp_handle *h, Coefs<T> &c, long long n) {
     T **ps[] = {&c.wW, &c.wE, &c.wS, &c.wN, &c.wET, &c.wNT, &c.wWT, &c.wST, &c.lf, &c.lg, &c.lh, &c.lfT, &c.lgT, &c.lhT};
     for (T **p : ps) {
-        TRY(dalloc(p, n));
-        if (cudaMemset(*p, 0, sizeof(T) * n) != cudaSuccess) return BLP_ERR_CUDA;
+        TRY(dalloc(h, p, n));
+        if (cudaMemsetAsync(*p, 0, sizeof(T) * n, h->stream) != cudaSuccess) return BLP_ERR_CUDA;
     }
     return BLP_OK;
 }
@@ -382,8 +456,8 @@ static int alloc_coefs(Coefs<T> &c, long long n) {
 template <typename T>
 static int make_pairs(blp_handle *h, const double *wE, const double *wN, const double *wET, const double *wNT,
                       typename Pair2<T>::type **pF, typename Pair2<T>::type **pR, long long n) {
-    TRY(dalloc(pF, n));
-    TRY(dalloc(pR, n));
+    TRY(dalloc(h, pF, n));
+    TRY(dalloc(h, pR, n));
     k_pack_pairs<T><<<grid_for(n, 256), 256, 0, h->stream>>>(wE, wN, *pF, n);
     LAUNCH_CHECK(h);
     k_pack_pairs<T><<<grid_for(n, 256), 256, 0, h->stream>>>(wET, wNT, *pR, n);
@@ -422,16 +496,16 @@ static int build_hierarchy(blp_handle *h) {
     int nlev = (int)ms.size();
     h->hd.nlev = h->hf.nlev = nlev;
     double *dxs = nullptr, *dys = nullptr;
-    TRY(dalloc(&dxs, L + 2));
-    TRY(dalloc(&dys, L + 2));
+    TRY(dalloc(h, &dxs, L + 2));
+    TRY(dalloc(h, &dys, L + 2));
     std::vector<double> xs(L + 2), ys(L + 2);
     for (int l = 0; l < nlev; l++) {
         int ml = ms[l], st = 1 << l;
         xs[0] = h->hx[0]; ys[0] = h->hy[0];
         for (int I = 1; I <= ml; I++) { xs[I] = h->hx[I * st]; ys[I] = h->hy[I * st]; }
         xs[ml + 1] = h->hx[L + 1]; ys[ml + 1] = h->hy[L + 1];
-        CUDA_TRY(cudaMemcpy(dxs, xs.data(), sizeof(double) * (ml + 2), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(dys, ys.data(), sizeof(double) * (ml + 2), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpyAsync(dxs, xs.data(), sizeof(double) * (ml + 2), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(dys, ys.data(), sizeof(double) * (ml + 2), cudaMemcpyHostToDevice, h->stream));
         Level<double> &D = h->hd.lev[l];
         Level<float> &F = h->hf.lev[l];
         D.R = F.R = make_region(LAYOUT_SKEW, ml, ml, 1, 1, 0);
@@ -439,10 +513,10 @@ static int build_hierarchy(blp_handle *h) {
         double **pd[] = {&D.wW, &D.wE, &D.wS, &D.wN, &D.wET, &D.wNT, &D.wWT, &D.wST, &D.omega, &D.dfe, &D.e[0], &D.e[1], &D.b};
         float **pf[] = {&F.wW, &F.wE, &F.wS, &F.wN, &F.wET, &F.wNT, &F.wWT, &F.wST, &F.omega, &F.dfe, &F.e[0], &F.e[1], &F.b};
         for (int q = 0; q < 13; q++) {
-            TRY(dalloc(pd[q], n));
-            TRY(dalloc(pf[q], n));
-            CUDA_TRY(cudaMemset(*pd[q], 0, sizeof(double) * n));
-            CUDA_TRY(cudaMemset(*pf[q], 0, sizeof(float) * n));
+            TRY(dalloc(h, pd[q], n));
+            TRY(dalloc(h, pf[q], n));
+            CUDA_TRY(cudaMemsetAsync(*pd[q], 0, sizeof(double) * n, h->stream));
+            CUDA_TRY(cudaMemsetAsync(*pf[q], 0, sizeof(float) * n, h->stream));
         }
         AsmOut o;
         memset(&o, 0, sizeof(o));
@@ -464,14 +538,14 @@ static int build_hierarchy(blp_handle *h) {
         }
         TRY(make_pairs<double>(h, D.wE, D.wN, D.wET, D.wNT, &D.pF, &D.pR, n));
         TRY(make_pairs<float>(h, D.wE, D.wN, D.wET, D.wNT, &F.pF, &F.pR, n));
-        TRY(dalloc(&D.beta, n));
-        TRY(dalloc(&F.beta, n));
-        CUDA_TRY(cudaMemset(D.beta, 0, sizeof(double) * n));
-        CUDA_TRY(cudaMemset(F.beta, 0, sizeof(float) * n));
+        TRY(dalloc(h, &D.beta, n));
+        TRY(dalloc(h, &F.beta, n));
+        CUDA_TRY(cudaMemsetAsync(D.beta, 0, sizeof(double) * n, h->stream));
+        CUDA_TRY(cudaMemsetAsync(F.beta, 0, sizeof(float) * n, h->stream));
         if (ml <= BLP_COARSE_MAX) {
             const long long nn = 10LL * ml * ml;
-            TRY(dalloc(&D.nat, nn));
-            TRY(dalloc(&F.nat, nn));
+            TRY(dalloc(h, &D.nat, nn));
+            TRY(dalloc(h, &F.nat, nn));
             NatSrc src = {{D.wW, D.wE, D.wS, D.wN, D.wET, D.wWT, D.wNT, D.wST, D.omega, D.dfe}};
             k_to_natural<<<grid_for((long long)ml * ml, 256), 256, 0, h->stream>>>(D.R, src, D.nat);
             LAUNCH_CHECK(h);
@@ -480,8 +554,8 @@ static int build_hierarchy(blp_handle *h) {
         }
         CUDA_TRY(cudaStreamSynchronize(h->stream));
     }
-    cudaFree(dxs);
-    cudaFree(dys);
+    blp_internal_free(h, dxs);
+    blp_internal_free(h, dys);
     return BLP_OK;
 }
 
@@ -497,23 +571,23 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
     h->hy.resize(N + 1);
     h->tau_x = blp_mesh(N, p.eps, p.sigma, p.beta_x, h->hx.data());
     h->tau_y = blp_mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
-    TRY(dalloc(&h->x, N + 1));
-    TRY(dalloc(&h->y, N + 1));
-    CUDA_TRY(cudaMemcpy(h->x, h->hx.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(h->y, h->hy.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice));
-    TRY(dalloc(&h->c1, n));
-    TRY(dalloc(&h->c2, n));
-    TRY(dalloc(&h->r, n));
+    TRY(dalloc(h, &h->x, N + 1));
+    TRY(dalloc(h, &h->y, N + 1));
+    CUDA_TRY(cudaMemcpyAsync(h->x, h->hx.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->y, h->hy.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice, h->stream));
+    TRY(dalloc(h, &h->c1, n));
+    TRY(dalloc(h, &h->c2, n));
+    TRY(dalloc(h, &h->r, n));
     CUDA_TRY(cudaMemcpyAsync(h->c1, c1, sizeof(double) * n, cudaMemcpyDefault, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->c2, c2, sizeof(double) * n, cudaMemcpyDefault, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->r, r, sizeof(double) * n, cudaMemcpyDefault, h->stream));
-    TRY(dalloc(&h->partials, BLP_SCALARS_OFF + 64));
-    TRY(dalloc(&h->dev, 1));
-    TRY(dalloc(&h->err, 4));
-    CUDA_TRY(cudaMemset(h->dev, 0, sizeof(DevState)));
-    CUDA_TRY(cudaMemset(h->err, 0, sizeof(int) * 4));
-    if (cudaMallocHost((void **)&h->host_state, sizeof(DevState)) != cudaSuccess) { cudaGetLastError(); return BLP_ERR_MEM; }
-    for (int q = 0; q < 4; q++) TRY(dalloc(&h->stage[q], n));
+    TRY(dalloc(h, &h->partials, BLP_SCALARS_OFF + 64));
+    TRY(dalloc(h, &h->dev, 1));
+    TRY(dalloc(h, &h->err, 4));
+    CUDA_TRY(cudaMemsetAsync(h->dev, 0, sizeof(DevState), h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream));
+    if (!(h->host_state = pinned_get())) return BLP_ERR_MEM;
+    for (int q = 0; q < 4; q++) TRY(dalloc(h, &h->stage[q], n));
 
     if (p.check_coefficients) {
         int nb = 128;
@@ -528,14 +602,14 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         double m0 = 1e300, m1 = 1e300, m2 = 1e300;
         for (int b = 0; b < nb; b++) { m0 = fmin(m0, mins[3 * b]); m1 = fmin(m1, mins[3 * b + 1]); m2 = fmin(m2, mins[3 * b + 2]); }
-        CUDA_TRY(cudaMemset(nf, 0, sizeof(int)));
+        CUDA_TRY(cudaMemsetAsync(nf, 0, sizeof(int), h->stream));
         if (nonfinite || m0 < 0.0 || m1 < 0.0 || m2 < 0.0) return BLP_ERR_COEF;
     }
 
-    TRY(dalloc(&h->aC, np));
-    CUDA_TRY(cudaMemset(h->aC, 0, sizeof(double) * np));
-    TRY(alloc_coefs(h->cd, np));
-    TRY(alloc_coefs(h->cf, np));
+    TRY(dalloc(h, &h->aC, np));
+    CUDA_TRY(cudaMemsetAsync(h->aC, 0, sizeof(double) * np, h->stream));
+    TRY(alloc_coefs(h, h->cd, np));
+    TRY(alloc_coefs(h, h->cf, np));
     AsmOut o;
     memset(&o, 0, sizeof(o));
     o.use_layout = 1; o.lay = h->lay; o.aC = h->aC;
@@ -559,7 +633,8 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
     return BLP_OK;
 }
 
-extern "C" int blp_setup(const blp_params *p, const double *c1, const double *c2, const double *r, blp_handle **out) {
+int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, const double *r, cudaStream_t stream,
+                       blp_handle **out) {
     if (!out) return BLP_ERR_ARG;
     *out = nullptr;
     if (!p || !c1 || !c2 || !r) return BLP_ERR_ARG;
@@ -574,7 +649,7 @@ extern "C" int blp_setup(const blp_params *p, const double *c1, const double *c2
     // tuning override: CTAs per wavefront cluster (1 = single-SM wavefront)
     if (const char *e = getenv("BLP_DTS_CLUSTER")) h->dts_max_cluster = std::max(1, std::min(8, atoi(e)));
     if (const char *e = getenv("BLP_DTS_CHUNK")) h->dts_chunk = atoi(e) == 8 ? 8 : 16;
-    h->stream = 0;
+    h->stream = stream;
     int rc = setup_impl(h, c1, c2, r);
     if (rc != BLP_OK) {
         blp_destroy(h);
@@ -583,6 +658,10 @@ extern "C" int blp_setup(const blp_params *p, const double *c1, const double *c2
     h->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h;
     return BLP_OK;
+}
+
+extern "C" int blp_setup(const blp_params *p, const double *c1, const double *c2, const double *r, blp_handle **out) {
+    return blp_internal_setup(p, c1, c2, r, 0, out);
 }
 
 // Debug/inspection helpers for the host-side layout tests (no GPU needed).
