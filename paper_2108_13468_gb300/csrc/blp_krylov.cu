@@ -3,6 +3,8 @@
 // preconditioner, the adjoint solve and the gradient assembly; C-ABI entry
 // points.
 #include "blp_common.cuh"
+#include <cstdint>
+#include <type_traits>
 #include <cmath>
 #include <chrono>
 #include <algorithm>
@@ -36,24 +38,41 @@ __global__ void k_matvec(Layout lay, Coefs<TC> c, const TX *__restrict__ x, TO *
     }
 }
 
-// partial[blk*MAXV + i] = sum_k V_i[k] * w[k], i < nv (per-thread sums in T,
-// block sums and everything after in FP64; deterministic order)
-template <typename T>
+// partial[blk*MAXV + i] = sum_k V_i[k] * w[k], i < nv <= NV (per-thread sums
+// in T, block sums and everything after in FP64; deterministic order).  NV is
+// the power-of-two bucket of nv, so the accumulators stay in registers; with
+// VEC2 each thread reads two consecutive entries per vector (16-byte loads).
+template <typename T, int NV, bool VEC2>
 __global__ void __launch_bounds__(256) k_multidot(const T *__restrict__ V, long long ld, int nv,
                                                   const T *__restrict__ w, long long n, double *partials) {
-    T acc[MAXV - 1];
+    T acc[NV];
 #pragma unroll
-    for (int i = 0; i < MAXV - 1; i++) acc[i] = T(0);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const T wk = w[k];
+    for (int i = 0; i < NV; i++) acc[i] = T(0);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (VEC2) {
+        typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
+        const T2 *w2 = reinterpret_cast<const T2 *>(w);
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n / 2; k += stride) {
+            const T2 wk = w2[k];
 #pragma unroll
-        for (int i = 0; i < MAXV - 1; i++)
-            if (i < nv) acc[i] += V[i * ld + k] * wk;
+            for (int i = 0; i < NV; i++)
+                if (i < nv) {
+                    const T2 v = reinterpret_cast<const T2 *>(V + i * ld)[k];
+                    acc[i] += v.x * wk.x + v.y * wk.y;
+                }
+        }
+    } else {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
+            const T wk = w[k];
+#pragma unroll
+            for (int i = 0; i < NV; i++)
+                if (i < nv) acc[i] += V[i * ld + k] * wk;
+        }
     }
-    __shared__ double sh[8][MAXV];
+    __shared__ double sh[8][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < MAXV - 1; i++) {
+    for (int i = 0; i < NV; i++) {
         if (i < nv) {
             double a = (double)acc[i];
             for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(FULL, a, off);
@@ -68,6 +87,24 @@ __global__ void __launch_bounds__(256) k_multidot(const T *__restrict__ V, long 
     }
 }
 
+template <typename T>
+static void launch_multidot(blp_handle *h, int nb, const T *V, long long ld, int nv, const T *w, long long n,
+                            double *partials) {
+    const bool v2 = (ld % 2 == 0) && (n % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
+#define BLP_MD(NVB)                                                                                   \
+    do {                                                                                              \
+        if (v2) k_multidot<T, NVB, true><<<nb, 256, 0, h->stream>>>(V, ld, nv, w, n, partials);      \
+        else k_multidot<T, NVB, false><<<nb, 256, 0, h->stream>>>(V, ld, nv, w, n, partials);        \
+    } while (0)
+    if (nv <= 2) BLP_MD(2);
+    else if (nv <= 4) BLP_MD(4);
+    else if (nv <= 8) BLP_MD(8);
+    else if (nv <= 16) BLP_MD(16);
+    else if (nv <= 32) BLP_MD(32);
+    else BLP_MD(MAXV - 1);
+#undef BLP_MD
+}
+
 // out[i] = sum_b partials[b*MAXV + i] (+ add[i] if add), one warp per entry
 __global__ void k_reduce(const double *partials, int nb, int nv, double *out, const double *add) {
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -80,19 +117,41 @@ __global__ void k_reduce(const double *partials, int nb, int nv, double *out, co
 }
 static inline int reduce_threads(int nv) { return 32 * (nv < 32 ? nv : 32); }
 
-// w -= sum_i V_i h_i ; optional partial sums of ||w||^2 into partials[blk*MAXV]
-template <typename T>
+// w -= sum_i V_i h_i ; optional partial sums of ||w||^2 into partials[blk*MAXV].
+// NV: power-of-two bucket of nv (coefficients in registers, loop unrolled);
+// VEC2: two consecutive entries per thread (16-byte loads and stores).
+template <typename T, int NV, bool VEC2>
 __global__ void __launch_bounds__(256) k_update(const T *__restrict__ V, long long ld, int nv, const double *__restrict__ h,
                                                 T *__restrict__ w, long long n, double *partials) {
-    __shared__ T hs[MAXV];
-    if (threadIdx.x < nv) hs[threadIdx.x] = (T)h[threadIdx.x];
-    __syncthreads();
+    T hc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; i++) hc[i] = i < nv ? (T)h[i] : T(0);
     T acc = T(0);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        T s = w[k];
-        for (int i = 0; i < nv; i++) s -= V[i * ld + k] * hs[i];
-        w[k] = s;
-        acc += s * s;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (VEC2) {
+        typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
+        T2 *w2 = reinterpret_cast<T2 *>(w);
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n / 2; k += stride) {
+            T2 s = w2[k];
+#pragma unroll
+            for (int i = 0; i < NV; i++)
+                if (i < nv) {
+                    const T2 v = reinterpret_cast<const T2 *>(V + i * ld)[k];
+                    s.x -= v.x * hc[i];
+                    s.y -= v.y * hc[i];
+                }
+            w2[k] = s;
+            acc += s.x * s.x + s.y * s.y;
+        }
+    } else {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
+            T s = w[k];
+#pragma unroll
+            for (int i = 0; i < NV; i++)
+                if (i < nv) s -= V[i * ld + k] * hc[i];
+            w[k] = s;
+            acc += s * s;
+        }
     }
     if (partials) {
         __shared__ double sh[8];
@@ -106,6 +165,24 @@ __global__ void __launch_bounds__(256) k_update(const T *__restrict__ V, long lo
             partials[blockIdx.x * MAXV] = s;
         }
     }
+}
+
+template <typename T>
+static void launch_update(blp_handle *h, int nb, const T *V, long long ld, int nv, const double *hv, T *w, long long n,
+                          double *partials) {
+    const bool v2 = (ld % 2 == 0) && (n % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
+#define BLP_UP(NVB)                                                                                   \
+    do {                                                                                              \
+        if (v2) k_update<T, NVB, true><<<nb, 256, 0, h->stream>>>(V, ld, nv, hv, w, n, partials);    \
+        else k_update<T, NVB, false><<<nb, 256, 0, h->stream>>>(V, ld, nv, hv, w, n, partials);      \
+    } while (0)
+    if (nv <= 2) BLP_UP(2);
+    else if (nv <= 4) BLP_UP(4);
+    else if (nv <= 8) BLP_UP(8);
+    else if (nv <= 16) BLP_UP(16);
+    else if (nv <= 32) BLP_UP(32);
+    else BLP_UP(MAXV - 1);
+#undef BLP_UP
 }
 
 // partial sums of ||x||^2 (and, with scale != null, of ||scale*x||^2 in slot 1)
@@ -354,22 +431,22 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
             int nv = j + 1;
             double *h1 = K.hbuf, *h2 = K.hbuf + MAXV, *nr = K.hbuf + 2 * MAXV;
             { ProfScope ps_(h, KC_MULTIDOT, (double)np * sizeof(double) * (nv + 1));
-              k_multidot<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
+              launch_multidot<double>(h, nb, K.V, np, nv, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
               k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
-              k_update<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h1, K.w, np, nullptr);
+              launch_update<double>(h, nb, K.V, np, nv, h1, K.w, np, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_MULTIDOT, (double)np * sizeof(double) * (nv + 1));
-              k_multidot<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, K.w, np, h->partials);
+              launch_multidot<double>(h, nb, K.V, np, nv, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
               k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
-              k_update<double><<<nb, 256, 0, h->stream>>>(K.V, np, nv, h2, K.w, np, h->partials);
+              launch_update<double>(h, nb, K.V, np, nv, h2, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
               k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr);
