@@ -465,9 +465,7 @@ static DtsShape dts_shape(int S, int max_cluster) {
     typedef DtsSmem<T, CH> SM;
     const size_t cap = 225 * 1024;
     DtsShape sh;
-    // small blocks (<= 4 strips) stay on one SM: their time is hand-off
-    // latency, which is lowest inside one CTA
-    sh.CL = S <= 4 ? 1 : std::max(1, std::min(max_cluster, S));
+    sh.CL = std::max(1, std::min(max_cluster, S));
     sh.WC = std::min(15, (S + sh.CL - 1) / sh.CL);
     sh.CL = std::min(sh.CL, (S + sh.WC - 1) / sh.WC);
     sh.NST = 16;
