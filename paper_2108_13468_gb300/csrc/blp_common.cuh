@@ -241,6 +241,20 @@ struct blp_handle {
     // standard-layout staging for host pointers
     double *stage[4] = {nullptr, nullptr, nullptr, nullptr};
     ProfState prof;
+    // captured preconditioner applications (see precond_apply): one graph per
+    // (precision, direction, corner batch), reading gv[prec] and writing gz[prec]
+    struct PrecGraph {
+        int trans, prec, batch, enq;
+        cudaGraphExec_t exec;
+        long long nlaunch;
+        int cur[BLP_MAXLEV];
+        bool zero[BLP_MAXLEV];
+    };
+    std::vector<PrecGraph> graphs;
+    void *gv[2] = {nullptr, nullptr}, *gz[2] = {nullptr, nullptr};
+    bool use_graphs = true;
+    bool warm[2][2] = {{false, false}, {false, false}};   // [prec][trans]: one eager application first
+    cudaStream_t own_stream = nullptr;   // capturable stream used when the caller's stream is the legacy one
 };
 
 // Stream-ordered device allocation from the library pool (handle's stream).

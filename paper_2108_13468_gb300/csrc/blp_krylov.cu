@@ -588,11 +588,38 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     return status;
 }
 
+// The legacy default stream cannot be captured into graphs: a solve issued
+// on it runs on a private non-blocking stream of the handle instead, ordered
+// after the caller's earlier work by an event.  The call returns after the
+// work has completed, as on any other stream.
+static int solve_on_capturable_stream(blp_handle *h, const double *f, double *u, double tol, blp_info *info, int trans) {
+    if (!h) return BLP_ERR_ARG;
+    if (h->stream != 0 || !h->use_graphs) return solve_common(h, f, u, tol, info, trans);
+    if (!h->own_stream) {
+        if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            h->own_stream = nullptr;
+            return solve_common(h, f, u, tol, info, trans);
+        }
+    }
+    cudaEvent_t ev;
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->own_stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return BLP_ERR_CUDA;
+    h->stream = h->own_stream;
+    int rc = solve_common(h, f, u, tol, info, trans);
+    cudaStreamSynchronize(h->own_stream);
+    h->stream = 0;
+    return rc;
+}
+
 extern "C" int blp_solve(blp_handle *h, const double *f, double *u, double tol, blp_info *info) {
-    return solve_common(h, f, u, tol, info, 0);
+    return solve_on_capturable_stream(h, f, u, tol, info, 0);
 }
 extern "C" int blp_solve_adjoint(blp_handle *h, const double *g, double *lambda, double tol, blp_info *info) {
-    return solve_common(h, g, lambda, tol, info, 1);
+    return solve_on_capturable_stream(h, g, lambda, tol, info, 1);
 }
 
 // ---------------------------------------------------------------------------

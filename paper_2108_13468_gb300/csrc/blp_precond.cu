@@ -1358,7 +1358,67 @@ struct Cycler {
 };
 
 // M_CC^{-1} b0 (or M_CC^{-T} b0) by the stationary multigrid iteration from
-// e = 0; the result is left in the returned level-0 buffer.
+// e = 0; the result is left in the returned level-0 buffer.  The iteration
+// is enqueued in two parts: corner_front (the initial norm and a batch of
+// cycles, each ending with the stopping test that sets the device skip flag
+// -- no host synchronisation, so it can be captured in a graph) and
+// corner_rest (read the flag; more cycles while the test fails).
+template <typename T, bool TRANS>
+static int corner_more(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int count, int *enq) {
+    Hierarchy<T> &H = hier_of<T>(h);
+    Level<T> &L0 = H.lev[0];
+    const int nb = 148;
+    const double red2 = h->p.corner_reduction * h->p.corner_reduction;
+    int *done = h->dev->flags;
+    for (int c = 0; c < count && *enq < h->p.corner_max_cycles; c++, (*enq)++) {
+        int rc = cy.vcycle(0);
+        if (rc) return rc;
+        ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 7 * sizeof(T));
+        k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[cy.cur[0]], 1, h->partials, done);
+        LAUNCH_CHECK(h);
+        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles);
+        LAUNCH_CHECK(h);
+    }
+    return BLP_OK;
+}
+
+template <typename T, bool TRANS>
+static int corner_front(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int batch, int *enq) {
+    Hierarchy<T> &H = hier_of<T>(h);
+    Level<T> &L0 = H.lev[0];
+    for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
+    cy.zero[0] = true;
+    CUDA_TRY(cudaMemsetAsync(L0.e[0], 0, sizeof(T) * L0.R.size, h->stream));
+    const int nb = 148;
+    const double red2 = h->p.corner_reduction * h->p.corner_reduction;
+    int *done = h->dev->flags;   // flags[0]
+    cy.skip = nullptr;
+    {
+        ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 2 * sizeof(T));
+        k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
+        LAUNCH_CHECK(h);
+        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles);
+        LAUNCH_CHECK(h);
+    }
+    cy.skip = done;
+    *enq = 0;
+    return corner_more(h, b0, cy, batch, enq);
+}
+
+template <typename T, bool TRANS>
+static int corner_rest(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int *enq, int *cycles) {
+    for (;;) {
+        CUDA_TRY(cudaMemcpyAsync(h->host_state, h->dev, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (h->host_state->flags[0] || *enq >= h->p.corner_max_cycles) break;
+        int rc = corner_more(h, b0, cy, 2, enq);
+        if (rc) return rc;
+    }
+    *cycles = h->host_state->flags[1];
+    h->last_cycles = *cycles + 1;
+    return BLP_OK;
+}
+
 template <typename T, bool TRANS>
 static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out) {
     Hierarchy<T> &H = hier_of<T>(h);
@@ -1372,57 +1432,159 @@ static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out)
     }
     Cycler<T, TRANS> cy;
     cy.h = h; cy.H = &H; cy.b0 = b0; cy.l0c = l0c;
-    for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
-    cy.zero[0] = true;
     Level<T> &L0 = H.lev[0];
-    CUDA_TRY(cudaMemsetAsync(L0.e[0], 0, sizeof(T) * L0.R.size, h->stream));
     const int fixed = h->p.corner_fixed_cycles;
     int cycles = 0;
     if (fixed > 0) {
+        for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
+        cy.zero[0] = true;
+        CUDA_TRY(cudaMemsetAsync(L0.e[0], 0, sizeof(T) * L0.R.size, h->stream));
         cy.skip = nullptr;
         for (int c = 0; c < fixed; c++) { int rc = cy.vcycle(0); if (rc) return rc; }
         cycles = fixed;
     } else {
-        int *done = h->dev->flags;   // flags[0]
-        const int nb = 148;
-        const double red2 = h->p.corner_reduction * h->p.corner_reduction;
-        cy.skip = nullptr;
-        {
-            ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 2 * sizeof(T));
-            k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
-            LAUNCH_CHECK(h);
-            k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles);
-            LAUNCH_CHECK(h);
-        }
-        cy.skip = done;
-        int batch = std::max(2, std::min(h->last_cycles > 0 ? h->last_cycles : 6, h->p.corner_max_cycles));
-        int enq = 0;
-        for (;;) {
-            for (int c = 0; c < batch && enq < h->p.corner_max_cycles; c++, enq++) {
-                int rc = cy.vcycle(0);
-                if (rc) return rc;
-                ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 7 * sizeof(T));
-                k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[cy.cur[0]], 1, h->partials, done);
-                LAUNCH_CHECK(h);
-                k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles);
-                LAUNCH_CHECK(h);
-            }
-            CUDA_TRY(cudaMemcpyAsync(h->host_state, h->dev, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
-            CUDA_TRY(cudaStreamSynchronize(h->stream));
-            if (h->host_state->flags[0] || enq >= h->p.corner_max_cycles) break;
-            batch = 2;
-        }
-        cycles = h->host_state->flags[1];
-        h->last_cycles = cycles + 1;
+        int enq = 0, rc;
+        const int batch = std::max(2, std::min(h->last_cycles > 0 ? h->last_cycles : 6, h->p.corner_max_cycles));
+        if ((rc = corner_front<T, TRANS>(h, b0, cy, batch, &enq))) return rc;
+        if ((rc = corner_rest<T, TRANS>(h, b0, cy, &enq, &cycles))) return rc;
     }
     *result = L0.e[cy.cur[0]];
     if (cycles_out) *cycles_out = cycles;
     return BLP_OK;
 }
 
-// z = (D^-1 M)^-1 v, or (D^-1 M)^-T v, both in the region-major layout.
+// The front of one application -- for the forward map the interior sweep,
+// the line chains, the corner right-hand side and the corner_front batch;
+// for the transposed map the corner_front batch -- is enqueued with no host
+// synchronisation.  On a capturable stream it is captured once per
+// (precision, direction, corner batch) as a CUDA graph that reads and
+// writes two fixed buffers of the handle, and replayed: two copies and one
+// launch instead of about a hundred launches.
+template <typename T>
+static int precond_front(blp_handle *h, const T *v, T *z, int trans, Cycler<T, false> &cf, Cycler<T, true> &ct,
+                         int batch, int *enq) {
+    Coefs<T> &c = coefs_of<T>(h);
+    Hierarchy<T> &H = hier_of<T>(h);
+    const Layout &lay = h->lay;
+    const Region &C = lay.R[0];
+    int rc;
+    if (!trans) {
+        DtsArgs<T> a;
+        a.R = lay.R[3]; a.beta = v; a.pair = c.pF; a.out = z;
+        a.bnd = nullptr; a.lay = lay; a.skip = nullptr; a.err = h->err;
+        if ((rc = launch_dts<T, false>(h, a, KC_DTS_INTERIOR))) return rc;
+        if ((rc = launch_chains<T, false>(h, c, v, z, nullptr))) return rc;
+        T *b0 = H.lev[0].b;
+        {
+            ProfScope ps(h, KC_LAYOUT);
+            k_corner_rhs<T><<<grid_for(C.size, 256), 256, 0, h->stream>>>(lay, v, z, c.wE, c.wN, b0, nullptr);
+            LAUNCH_CHECK(h);
+        }
+        return corner_front<T, false>(h, b0, cf, batch, enq);
+    }
+    return corner_front<T, true>(h, v + C.off, ct, batch, enq);
+}
+
+template <typename T>
+static int precond_graph(blp_handle *h, const T *v_in, T *z_out, int trans, int *cycles) {
+    Hierarchy<T> &H = hier_of<T>(h);
+    const Layout &lay = h->lay;
+    const Region &C = lay.R[0];
+    const int prec = sizeof(T) == 4 ? 1 : 0;
+    const size_t bytes = sizeof(T) * (size_t)lay.npad;
+    int rc;
+    if (!h->gv[prec]) {
+        if ((rc = blp_internal_alloc(h, &h->gv[prec], bytes))) return rc;
+        if ((rc = blp_internal_alloc(h, &h->gz[prec], bytes))) return rc;
+        CUDA_TRY(cudaMemsetAsync(h->gv[prec], 0, bytes, h->stream));
+        CUDA_TRY(cudaMemsetAsync(h->gz[prec], 0, bytes, h->stream));
+    }
+    const T *v = static_cast<const T *>(h->gv[prec]);
+    T *z = static_cast<T *>(h->gz[prec]);
+    CUDA_TRY(cudaMemcpyAsync(h->gv[prec], v_in, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    const int batch = std::max(2, std::min(h->last_cycles > 0 ? h->last_cycles : 6, h->p.corner_max_cycles));
+    Cycler<T, false> cf;
+    Cycler<T, true> ct;
+    cf.h = ct.h = h; cf.H = ct.H = &H; cf.l0c = ct.l0c = coarse_start(H);
+    cf.b0 = H.lev[0].b;
+    ct.b0 = v + C.off;
+    blp_handle::PrecGraph *G = nullptr;
+    for (auto &g : h->graphs)
+        if (g.trans == trans && g.prec == prec && g.batch == batch) { G = &g; break; }
+    if (!G) {
+        blp_handle::PrecGraph g;
+        memset(&g, 0, sizeof(g));
+        g.trans = trans; g.prec = prec; g.batch = batch;
+        const long long l0 = h->launches;
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int enq = 0;
+        rc = precond_front<T>(h, v, z, trans, cf, ct, batch, &enq);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (rc != BLP_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            h->use_graphs = false;
+            return rc != BLP_OK ? rc : BLP_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->use_graphs = false;
+            return BLP_ERR_CUDA;
+        }
+        g.nlaunch = h->launches - l0;
+        h->launches = l0;
+        g.enq = enq;
+        for (int l = 0; l < BLP_MAXLEV; l++) {
+            g.cur[l] = trans ? ct.cur[l] : cf.cur[l];
+            g.zero[l] = trans ? ct.zero[l] : cf.zero[l];
+        }
+        h->graphs.push_back(g);
+        G = &h->graphs.back();
+    }
+    CUDA_TRY(cudaGraphLaunch(G->exec, h->stream));
+    h->launches += G->nlaunch;
+    // continue the corner iteration from the captured state if its test failed
+    int enq = G->enq, cyc = 0;
+    int *done = h->dev->flags;
+    T *e = nullptr;
+    if (!trans) {
+        for (int l = 0; l < BLP_MAXLEV; l++) { cf.cur[l] = G->cur[l]; cf.zero[l] = G->zero[l]; }
+        cf.skip = done;
+        if ((rc = corner_rest<T, false>(h, cf.b0, cf, &enq, &cyc))) return rc;
+        e = H.lev[0].e[cf.cur[0]];
+    } else {
+        for (int l = 0; l < BLP_MAXLEV; l++) { ct.cur[l] = G->cur[l]; ct.zero[l] = G->zero[l]; }
+        ct.skip = done;
+        if ((rc = corner_rest<T, true>(h, ct.b0, ct, &enq, &cyc))) return rc;
+        e = H.lev[0].e[ct.cur[0]];
+    }
+    {
+        ProfScope ps(h, KC_LAYOUT);
+        CUDA_TRY(cudaMemcpyAsync(z + C.off, e, sizeof(T) * C.size, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (trans) {
+        Coefs<T> &c = coefs_of<T>(h);
+        if ((rc = launch_chains<T, true>(h, c, v, z, nullptr))) return rc;
+        DtsArgs<T> a;
+        a.R = lay.R[3]; a.beta = v; a.pair = c.pR; a.out = z;
+        a.bnd = z; a.lay = lay; a.skip = nullptr; a.err = h->err;
+        if ((rc = launch_dts<T, true>(h, a, KC_DTS_INTERIOR))) return rc;
+    }
+    CUDA_TRY(cudaMemcpyAsync(z_out, z, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (cycles) *cycles = cyc;
+    return BLP_OK;
+}
+
 template <typename T>
 int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles) {
+    const int prec = sizeof(T) == 4 ? 1 : 0;
+    if (h->use_graphs && h->warm[prec][trans ? 1 : 0] && h->stream != 0 && !h->prof.on &&
+        h->p.corner_fixed_cycles <= 0 && coarse_start(hier_of<T>(h)) > 0)
+        return precond_graph<T>(h, v, z, trans, cycles);
+    h->warm[prec][trans ? 1 : 0] = true;   // the first application runs eagerly (kernel attributes set outside any capture)
     Coefs<T> &c = coefs_of<T>(h);
     Hierarchy<T> &H = hier_of<T>(h);
     const Layout &lay = h->lay;

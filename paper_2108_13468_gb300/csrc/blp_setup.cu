@@ -348,6 +348,10 @@ extern "C" void blp_destroy(blp_handle *h) {
     free_hier(h, h->hf);
     blp_internal_prof_flush(h);
     for (auto &e : h->prof.ev) cudaEventDestroy(e);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    for (int q = 0; q < 2; q++) { blp_internal_free(h, h->gv[q]); blp_internal_free(h, h->gz[q]); }
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
     void *ps[] = {h->x, h->y, h->aC, h->c1, h->c2, h->r, h->partials, h->dev, h->err, h->ws,
                   h->stage[0], h->stage[1], h->stage[2], h->stage[3]};
     for (void *p : ps) blp_internal_free(h, p);
@@ -649,6 +653,7 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
     // tuning override: CTAs per wavefront cluster (1 = single-SM wavefront)
     if (const char *e = getenv("BLP_DTS_CLUSTER")) h->dts_max_cluster = std::max(1, std::min(8, atoi(e)));
     if (const char *e = getenv("BLP_DTS_CHUNK")) h->dts_chunk = atoi(e) == 8 ? 8 : 16;
+    if (const char *e = getenv("BLP_GRAPHS")) h->use_graphs = atoi(e) != 0;
     h->stream = stream;
     int rc = setup_impl(h, c1, c2, r);
     if (rc != BLP_OK) {
