@@ -920,9 +920,27 @@ __device__ __forceinline__ T level_residual(const Level<T> &Lv, const T *__restr
     return b[p] - s;
 }
 
+// Scaled fine residual of the restriction, one thread per fine node:
+// rr = omega_f (b - A e) (forward) or b - A^T e (transposed), zero on the
+// padding slots.
 template <typename T, bool TRANS>
-__global__ void k_mg_restrict(Level<T> F, const T *__restrict__ bf, const T *__restrict__ ef, Level<T> Cc,
-                              T *__restrict__ bc, T *__restrict__ ec, const int *skip) {
+__global__ void k_mg_residual(Level<T> F, const T *__restrict__ bf, const T *__restrict__ ef, T *__restrict__ rr,
+                              const int *skip) {
+    if (skip && *skip) return;
+    const Region &RF = F.R;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < RF.size; q += (long long)gridDim.x * blockDim.x) {
+        int a, bb;
+        if (!RF.coords(q, a, bb)) { rr[q] = T(0); continue; }
+        const T r = level_residual<T, TRANS>(F, bf, ef, a, bb);
+        rr[q] = TRANS ? r : r * F.omega[q];
+    }
+}
+
+// Restriction b_c = omega_c^-1 P^T rr (forward) or P^T rr (transposed): the
+// full-weighting stencil over the fine residuals around node (2A+1, 2B+1).
+template <typename T, bool TRANS>
+__global__ void k_mg_restrict(Level<T> F, const T *__restrict__ rr, Level<T> Cc, T *__restrict__ bc, T *__restrict__ ec,
+                              const int *skip) {
     if (skip && *skip) return;
     const Region &RC = Cc.R, &RF = F.R;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < RC.size; q += (long long)gridDim.x * blockDim.x) {
@@ -941,9 +959,7 @@ __global__ void k_mg_restrict(Level<T> F, const T *__restrict__ bf, const T *__r
                 const int a = a0 + da;
                 if (a < 0 || a >= RF.mx) continue;
                 const T wx = da == 0 ? T(1) : T(0.5);
-                T r = level_residual<T, TRANS>(F, bf, ef, a, bb);
-                if (!TRANS) r *= F.omega[RF.addr(a, bb)];
-                sum += wx * wy * r;
+                sum += wx * wy * rr[RF.addr(a, bb)];
             }
         }
         bc[q] = TRANS ? sum : sum / Cc.omega[q];
@@ -1338,9 +1354,12 @@ struct Cycler {
         if (rc) return rc;
         Level<T> &Cn = H->lev[l + 1];
         {
-            // fine b, e, 4 couplings, omega once each; coarse b written
-            ProfScope ps(h, KC_MG_RESTRICT, ((double)Lv.R.mx * Lv.R.my * 7 + (double)Cn.R.mx * Cn.R.my * 2) * sizeof(T));
-            k_mg_restrict<T, TRANS><<<grid_for(Cn.R.size, 256), 256, 0, h->stream>>>(Lv, b, Lv.e[cur[l]], Cn, Cn.b,
+            // fine b, e, 4 couplings, omega read and the residual written; then
+            // the residual read and coarse b (and e) written
+            ProfScope ps(h, KC_MG_RESTRICT, ((double)Lv.R.mx * Lv.R.my * 9 + (double)Cn.R.mx * Cn.R.my * 2) * sizeof(T));
+            k_mg_residual<T, TRANS><<<grid_for(Lv.R.size, 256), 256, 0, h->stream>>>(Lv, b, Lv.e[cur[l]], Lv.beta, skip);
+            LAUNCH_CHECK(h);
+            k_mg_restrict<T, TRANS><<<grid_for(Cn.R.size, 256), 256, 0, h->stream>>>(Lv, Lv.beta, Cn, Cn.b,
                                                                                     Cn.e[cur[l + 1]], skip);
             LAUNCH_CHECK(h);
         }
@@ -1367,7 +1386,7 @@ template <typename T, bool TRANS>
 static int corner_more(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int count, int *enq) {
     Hierarchy<T> &H = hier_of<T>(h);
     Level<T> &L0 = H.lev[0];
-    const int nb = 148;
+    const int nb = BLP_RED_BLOCKS;
     const double red2 = h->p.corner_reduction * h->p.corner_reduction;
     int *done = h->dev->flags;
     for (int c = 0; c < count && *enq < h->p.corner_max_cycles; c++, (*enq)++) {
@@ -1389,7 +1408,7 @@ static int corner_front(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int ba
     for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
     cy.zero[0] = true;
     CUDA_TRY(cudaMemsetAsync(L0.e[0], 0, sizeof(T) * L0.R.size, h->stream));
-    const int nb = 148;
+    const int nb = BLP_RED_BLOCKS;
     const double red2 = h->p.corner_reduction * h->p.corner_reduction;
     int *done = h->dev->flags;   // flags[0]
     cy.skip = nullptr;
