@@ -20,7 +20,7 @@
 // ---------------------------------------------------------------------------
 template <typename TC, typename TX, typename TO, bool TRANS>
 __global__ void k_matvec(Layout lay, Coefs<TC> c, const TX *__restrict__ x, TO *__restrict__ out,
-                         const TO *__restrict__ f, int mode) {
+                         const TO *__restrict__ f, int mode, const double *__restrict__ rs) {
     const int M = lay.N - 1;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < lay.npad; p += (long long)gridDim.x * blockDim.x) {
         int i, j;
@@ -34,7 +34,8 @@ __global__ void k_matvec(Layout lay, Coefs<TC> c, const TX *__restrict__ x, TO *
         if (i < M) s += ce * (TO)x[lay.addr(i + 1, j)];
         if (j > 1) s += cs * (TO)x[lay.addr(i, j - 1)];
         if (j < M) s += cn * (TO)x[lay.addr(i, j + 1)];
-        out[p] = mode ? f[p] - s : s;
+        const TO v = mode ? f[p] - s : s;
+        out[p] = rs ? v * (TO)rs[p] : v;   // rs = diag(A): the unscaled operator / residual
     }
 }
 
@@ -209,6 +210,15 @@ __global__ void __launch_bounds__(256) k_norm2(const T *__restrict__ x, long lon
 
 // y = alpha * x / s where s = *sdev (device scalar, sqrt applied if sq);
 // sdev == nullptr: y = alpha * x (precision conversion)
+// y = x / d elementwise (0 where d = 0: the padding slots of diag(A))
+template <typename TO>
+__global__ void k_div(const double *__restrict__ x, const double *__restrict__ d, TO *__restrict__ y, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double dk = d[k];
+        y[k] = (TO)(dk != 0.0 ? x[k] / dk : 0.0);
+    }
+}
+
 template <typename TI, typename TO>
 __global__ void k_scale(const TI *__restrict__ x, TO *__restrict__ y, long long n, const double *sdev, int sq, double alpha) {
     double f = alpha;
@@ -341,12 +351,13 @@ static int nblocks(long long np) { return (int)std::min<long long>(BLP_RED_BLOCK
 
 // out = Op x (mode 0) or f - Op x (mode 1); FP64 operator, x in TX precision
 template <typename TX>
-static int matvec(blp_handle *h, const TX *x, double *out, const double *f, int mode, int trans) {
+static int matvec(blp_handle *h, const TX *x, double *out, const double *f, int mode, int trans,
+                  const double *rs = nullptr) {
     long long np = h->lay.npad;
     const double nodes = (double)(h->N - 1) * (h->N - 1);
     ProfScope ps(h, KC_MATVEC, nodes * (sizeof(double) * (mode ? 6 : 5) + sizeof(TX)));   // x, 4 couplings, out (+ f)
-    if (trans) k_matvec<double, TX, double, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode);
-    else k_matvec<double, TX, double, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode);
+    if (trans) k_matvec<double, TX, double, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode, rs);
+    else k_matvec<double, TX, double, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode, rs);
     LAUNCH_CHECK(h);
     return BLP_OK;
 }
@@ -389,8 +400,13 @@ static int check_err(blp_handle *h) {
 // a restart whose true residual is <= target, or at maxit iterations (a
 // cycle also ends early when the Arnoldi estimate reaches the target).
 template <typename TZ>
+// rs == nullptr: Arnoldi on the row-normalised operator D^-1 A with right-hand
+// side b = D^-1 f.  rs == diag(A): Arnoldi on A itself (unscaled residuals,
+// the paper's formulation), with the same b: the residual f - A x is formed
+// as rs * (b - D^-1 A x), and the preconditioner, which maps v to
+// (D^-1 M)^-1 v = M^-1 D v, receives D^-1 v; vs is a scratch vector.
 static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int trans, double target, int maxit,
-                  int *iters, int *restarts, int *maxcyc, double *res_out) {
+                  int *iters, int *restarts, int *maxcyc, double *res_out, const double *rs, double *vs) {
     const long long np = K.np;
     const int m = K.m;
     int nb = nblocks(np);
@@ -399,7 +415,7 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
     double res = 0.0;
     for (;;) {
         // r = b - Op x -> V_0
-        if ((rc = matvec<double>(h, x, K.V, b, 1, trans))) return rc;
+        if ((rc = matvec<double>(h, x, K.V, b, 1, trans, rs))) return rc;
         if ((rc = norm2<double>(h, K.V, nullptr, K.hbuf + 3 * MAXV))) return rc;
         double beta2;
         if ((rc = read_doubles(h, K.hbuf + 3 * MAXV, &beta2, 1))) return rc;
@@ -418,15 +434,23 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
             TZ *zj = K.Z + j * np;
             int cyc = 0;
             if (sizeof(TZ) == sizeof(double)) {
-                if ((rc = precond_apply<TZ>(h, (const TZ *)vj, zj, trans, &cyc))) return rc;
+                const double *vin = vj;
+                if (rs) {
+                    { ProfScope ps_(h, KC_SMALL);
+                      k_div<double><<<grid_for(np, 256), 256, 0, h->stream>>>(vj, rs, vs, np);
+                      LAUNCH_CHECK(h); }
+                    vin = vs;
+                }
+                if ((rc = precond_apply<TZ>(h, (const TZ *)vin, zj, trans, &cyc))) return rc;
             } else {
                 { ProfScope ps_(h, KC_SMALL);
-                  k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(vj, K.v32, np, nullptr, 0, 1.0);
+                  if (rs) k_div<float><<<grid_for(np, 256), 256, 0, h->stream>>>(vj, rs, K.v32, np);
+                  else k_scale<double, float><<<grid_for(np, 256), 256, 0, h->stream>>>(vj, K.v32, np, nullptr, 0, 1.0);
                   LAUNCH_CHECK(h); }
                 if ((rc = precond_apply<float>(h, K.v32, (float *)zj, trans, &cyc))) return rc;
             }
             if (cyc > *maxcyc) *maxcyc = cyc;
-            if ((rc = matvec<TZ>(h, zj, K.w, nullptr, 0, trans))) return rc;
+            if ((rc = matvec<TZ>(h, zj, K.w, nullptr, 0, trans, rs))) return rc;
             // classical Gram-Schmidt, twice (mathematically the MGS step of Sec. 3.3)
             int nv = j + 1;
             double *h1 = K.hbuf, *h2 = K.hbuf + MAXV, *nr = K.hbuf + 2 * MAXV;
@@ -546,14 +570,21 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
         status = BLP_OK;
     } else {
         const int budget = h->p.maxit;
+        // in FP64 the unscaled stopping rules run Arnoldi on A itself, so that
+        // FGMRES minimises the residual in the norm it stops on (the paper's
+        // formulation, Sec. 3.3).  The scaled rule, the adjoint and the mixed
+        // path use D^-1 A: an FP32 preconditioner fed D^-1 v for unscaled v
+        // (entries spanning the diagonal's ~1e11 range) loses the layer rows.
+        const double *rs = (!trans && !mixed && mode != BLP_STOP_SCALED) ? h->aC : nullptr;
         while (!met(res_s, res_u) && iters < budget) {
-            // the Arnoldi estimate tracks the normalised residual; for the
-            // unscaled rules convert the target with the current ratio
-            double tgt = mode == BLP_STOP_SCALED ? target_scaled : target_unscaled * (res_s / std::max(res_u, 1e-300));
+            // without rs the Arnoldi estimate tracks the normalised residual:
+            // for the unscaled rules convert the target with the current ratio
+            double tgt = mode == BLP_STOP_SCALED ? target_scaled
+                                                 : (rs ? target_unscaled : target_unscaled * (res_s / std::max(res_u, 1e-300)));
             double dummy;
             int it0 = iters;
-            if (mixed) rc = fgmres<float>(h, W.kf, W.f, W.u, trans, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy);
-            else rc = fgmres<double>(h, W.kd, W.f, W.u, trans, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy);
+            if (mixed) rc = fgmres<float>(h, W.kf, W.f, W.u, trans, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy, rs, W.t);
+            else rc = fgmres<double>(h, W.kd, W.f, W.u, trans, tgt, budget - iters, &iters, &restarts, &maxcyc, &dummy, rs, W.t);
             if (rc != BLP_OK && rc != BLP_ERR_NOCONV) return rc;
             if ((rc = true_res(res_s, res_u))) return rc;
             if (iters == it0) break;

@@ -82,6 +82,24 @@ def problem_fourier_trig(x, y, N, eps, seed=2) -> Problem:
     return Problem(N, eps, c1, c2, r, fourier_rhs(x, y, fourier_coeffs(seed)))
 
 
+def mms_exponential(x, y, eps):
+    """Manufactured problem of Sec. 3.3, eq. (exponential_MMS): c1 = 2,
+    c2 = 3, r = 1 and u = cos(pi x/2)(1 - e^{-2x/eps})(1-y)^3(1 - e^{-3y/eps});
+    returns (f, u) at the interior nodes, f = -eps Lap u - 2 u_x - 3 u_y + u
+    written out by the product rule."""
+    X, Y = interior_grid(x, y)
+    ex, ey = np.exp(-2.0 * X / eps), np.exp(-3.0 * Y / eps)
+    a, a1, a2 = np.cos(np.pi * X / 2), -np.pi / 2 * np.sin(np.pi * X / 2), -np.pi ** 2 / 4 * np.cos(np.pi * X / 2)
+    b, b1, b2 = 1.0 - ex, 2.0 / eps * ex, -4.0 / eps ** 2 * ex
+    c, c1, c2 = (1.0 - Y) ** 3, -3.0 * (1.0 - Y) ** 2, 6.0 * (1.0 - Y)
+    d, d1, d2 = 1.0 - ey, 3.0 / eps * ey, -9.0 / eps ** 2 * ey
+    Xf, Xf1, Xf2 = a * b, a1 * b + a * b1, a2 * b + 2 * a1 * b1 + a * b2
+    Yf, Yf1, Yf2 = c * d, c1 * d + c * d1, c2 * d + 2 * c1 * d1 + c * d2
+    u = Xf * Yf
+    f = -eps * (Xf2 * Yf + Xf * Yf2) - 2.0 * Xf1 * Yf - 3.0 * Xf * Yf1 + u
+    return f, u
+
+
 def batch_params(count: int = 256, seed: int = 3, n_choices=tuple(range(64, 513, 32)),
                  log_eps=(-8.0, -2.0)):
     """Per-instance (N, eps, a, b, fourier seed) for the batched workload:
