@@ -150,6 +150,9 @@ struct Coefs {
     T *wET = nullptr, *wNT = nullptr, *wWT = nullptr, *wST = nullptr;
     T *lf = nullptr, *lg = nullptr, *lh = nullptr;
     T *lfT = nullptr, *lgT = nullptr, *lhT = nullptr;
+    // multipliers of the line-chain scans, precomputed per line and thread
+    // (forward / transposed chains); null where the chain kernel does not use them
+    T *cpre = nullptr, *cpreT = nullptr;
 };
 
 // One level of the corner multigrid hierarchy (Sec. 3.2): a standalone
@@ -260,6 +263,8 @@ struct blp_handle {
 // Stream-ordered device allocation from the library pool (handle's stream).
 int blp_internal_alloc(blp_handle *h, void **p, size_t bytes);
 void blp_internal_free(blp_handle *h, void *p);
+// Precompute the line-chain scan multipliers of both precisions (setup).
+int blp_internal_chain_pre(blp_handle *h);
 // blp_setup with the handle's work issued on `stream` from the start.
 int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, const double *r, cudaStream_t stream,
                        blp_handle **out);

@@ -584,6 +584,74 @@ __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&
     __syncthreads();
 }
 
+// The multipliers of block_affine_scan do not depend on the right-hand side:
+// thread t's product M of its KPT multipliers (scan order), the M it holds
+// before each of the five Kogge-Stone levels, its final M (the warp total on
+// the last lane) and its neighbour's final M.  scan_multipliers computes the
+// seven values with exactly the products block_affine_scan forms;
+// block_affine_scan_pre then runs the A part of the same scan with them.
+template <typename T, int KPT, bool BACK>
+__device__ __forceinline__ void scan_multipliers(const T (&mu)[KPT], T (&pre)[7]) {
+    const int lane = threadIdx.x & 31;
+    T M = T(1);
+#pragma unroll
+    for (int q = 0; q < KPT; q++) {
+        const int e = BACK ? KPT - 1 - q : q;
+        M = mu[e] * M;
+    }
+    int lvl = 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        pre[lvl++] = M;
+        const T Mp = BACK ? __shfl_down_sync(FULL, M, off) : __shfl_up_sync(FULL, M, off);
+        const bool ok = BACK ? (lane + off < 32) : (lane >= off);
+        if (ok) M = M * Mp;
+    }
+    pre[5] = M;
+    pre[6] = BACK ? __shfl_down_sync(FULL, M, 1) : __shfl_up_sync(FULL, M, 1);
+}
+
+template <typename T, int KPT, bool BACK>
+__device__ __forceinline__ void block_affine_scan_pre(const T (&al)[KPT], const T (&mu)[KPT], const T (&pre)[7],
+                                                      T (&x)[KPT], T *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T A = T(0);
+#pragma unroll
+    for (int q = 0; q < KPT; q++) {
+        const int e = BACK ? KPT - 1 - q : q;
+        A = al[e] + mu[e] * A;
+    }
+    int lvl = 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T Ap = BACK ? __shfl_down_sync(FULL, A, off) : __shfl_up_sync(FULL, A, off);
+        const bool ok = BACK ? (lane + off < 32) : (lane >= off);
+        if (ok) A = A + pre[lvl] * Ap;
+        lvl++;
+    }
+    const int last = BACK ? 0 : 31;
+    if (nw > 1) {
+        if (lane == last) { sh[wid] = A; sh[32 + wid] = pre[5]; }
+        __syncthreads();
+    }
+    T carry = T(0);
+    if (BACK) {
+        for (int v = nw - 1; v > wid; v--) carry = sh[v] + sh[32 + v] * carry;
+    } else {
+        for (int v = 0; v < wid; v++) carry = sh[v] + sh[32 + v] * carry;
+    }
+    const T Aprev = BACK ? __shfl_down_sync(FULL, A, 1) : __shfl_up_sync(FULL, A, 1);
+    const bool first = BACK ? (lane == 31) : (lane == 0);
+    T xin = first ? carry : Aprev + pre[6] * carry;
+#pragma unroll
+    for (int q = 0; q < KPT; q++) {
+        const int e = BACK ? KPT - 1 - q : q;
+        xin = al[e] + mu[e] * xin;
+        x[e] = xin;
+    }
+    if (nw > 1) __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Line chains (Sec. 3.1): block 0 = Y block (lines of constant x, solved
 // right to left, keeping the E coupling to the line solved before and, on
@@ -603,6 +671,8 @@ struct ChainArgs {
     T *z;
     const T *wE, *wN, *wET, *wNT;
     const T *lf, *lg, *lh;
+    const T *pre;   // precomputed scan multipliers of this direction (k_line_chain2)
+    int nlmax;      // lines per block in the pre layout
     const int *skip;
 };
 
@@ -695,12 +765,13 @@ __global__ void __launch_bounds__(512) k_line_chain(ChainArgs<T> A) {
 // [t*KPT, t*KPT+KPT) of a line; each such segment is followed by 16 bytes
 // of padding, so the 16-byte vector reads of a warp hit distinct banks.
 // NW = 1 keeps both scans inside one warp (no CTA barrier).
-template <typename T, int KPT, int NW>
+template <typename T, int KPT, int NW, bool USEPRE>
 struct ChainSmem {
     static constexpr int VEC = 16 / sizeof(T);         // elements per 16 bytes
     static constexpr int LP = 32 * NW * KPT;           // padded line length
     static constexpr int LPP = LP / KPT * (KPT + VEC);  // with 16 bytes after each segment
-    static constexpr size_t stage_elems = (size_t)5 * LPP + VEC;
+    static constexpr int PRE = USEPRE ? 14 * 32 * NW : 0;   // scan multipliers: 2 scans x 7 per thread
+    static constexpr size_t stage_elems = (size_t)5 * LPP + VEC + PRE;
     static constexpr size_t stage = stage_elems * sizeof(T);
     static __device__ __forceinline__ int at(int e) { return e / KPT * (KPT + VEC) + e % KPT; }
 };
@@ -722,9 +793,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T, int KPT, int NW, int NS, bool TRANS>
+template <typename T, int KPT, int NW, int NS, bool TRANS, bool USEPRE>
 __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
-    typedef ChainSmem<T, KPT, NW> SM;
+    typedef ChainSmem<T, KPT, NW, USEPRE> SM;
     constexpr int VEC = SM::VEC, NV = KPT / VEC;
     typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
     if (A.skip && *A.skip) return;
@@ -761,6 +832,11 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
                 const long long pi = isY ? I.addr(line, 0) : I.addr(0, line);
                 cp_async_word(st + 5 * SM::LPP, bcpl + base + (L - 1));
                 cp_async_word(st + 5 * SM::LPP + 1, A.z + pi);
+            }
+            if (USEPRE) {   // this line's scan multipliers: 14 values per thread, contiguous
+                const T *pre = A.pre + (size_t)(blockIdx.x * A.nlmax + line) * SM::PRE;
+                T *spre = st + 5 * SM::LPP + VEC;
+                for (int k = tid; k < SM::PRE / VEC; k += nthr) cp_async_16(spre + k * VEC, pre + k * VEC);
             }
         }
         cp_async_commit();
@@ -805,10 +881,24 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
                 al[q] = T(0); mu[q] = T(1); g[q] = T(0); hh[q] = T(1);
             }
         }
-        block_affine_scan<T, KPT, false>(al, mu, y, sh);
+        if constexpr (USEPRE) {
+            T pf[7], pbk[7];
+            const T *spre = st + 5 * SM::LPP + VEC;
 #pragma unroll
-        for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
-        block_affine_scan<T, KPT, true>(al, mu, zp, sh);
+            for (int k = 0; k < 7; k++) {
+                pf[k] = spre[k * nthr + tid];
+                pbk[k] = spre[(7 + k) * nthr + tid];
+            }
+            block_affine_scan_pre<T, KPT, false>(al, mu, pf, y, sh);
+#pragma unroll
+            for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
+            block_affine_scan_pre<T, KPT, true>(al, mu, pbk, zp, sh);
+        } else {
+            block_affine_scan<T, KPT, false>(al, mu, y, sh);
+#pragma unroll
+            for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
+            block_affine_scan<T, KPT, true>(al, mu, zp, sh);
+        }
 #pragma unroll
         for (int r = 0; r < NV; r++)
             if (e0 + r * VEC < L) *reinterpret_cast<V *>(A.z + base + e0 + r * VEC) = *reinterpret_cast<const V *>(zp + r * VEC);
@@ -816,20 +906,100 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
     cp_async_wait<0>();
 }
 
+// Chain configuration (elements per thread, warps, stages) by line length
+// and precision, shared by the launch and the multiplier precomputation.
+template <int KPT_, int NW_, int NS_>
+struct ChainCfg { static constexpr int KPT = KPT_, NW = NW_, NS = NS_; };
+template <typename T, typename F>
+static int with_chain_cfg(int L, F &&f) {
+    if constexpr (sizeof(T) == 4) {
+        if (L <= 512) return f(ChainCfg<16, 1, 8>{});
+        if (L <= 1024) return f(ChainCfg<16, 2, 6>{});
+        return f(ChainCfg<16, 4, 3>{});
+    } else {
+        if (L <= 512) return f(ChainCfg<4, 4, 4>{});
+        if (L <= 1024) return f(ChainCfg<8, 4, 3>{});
+        return f(ChainCfg<16, 4, 2>{});
+    }
+}
+static bool chain2_applies(const blp_handle *h, size_t elem) {
+    return h->L <= 2048 && (h->L * elem) % 16 == 0 && (h->lay.R[1].off * elem) % 16 == 0 &&
+           (h->lay.R[2].off * elem) % 16 == 0;
+}
+
+// Setup: the scan multipliers of every line of both blocks, both scans, for
+// the forward (lf, lh) or transposed (lfT, lhT) chain.  One CTA per line.
+template <typename T, int KPT, int NW, bool TRANS>
+__global__ void __launch_bounds__(32 * NW) k_chain_pre(Layout lay, const T *__restrict__ lf, const T *__restrict__ lh,
+                                                       T *__restrict__ out, int nlmax) {
+    const bool isY = blockIdx.y == 0;
+    const int L = lay.L;
+    const Region &B = isY ? lay.R[2] : lay.R[1];
+    const int nlines = isY ? lay.R[2].mx : lay.R[1].my;
+    const int line = blockIdx.x;
+    if (line >= nlines) return;
+    const long long base = B.off + (long long)line * L;
+    const int tid = threadIdx.x, nthr = 32 * NW, e0 = tid * KPT;
+    T mf[KPT], mh[KPT], p0[7], p1[7];
+#pragma unroll
+    for (int q = 0; q < KPT; q++) {
+        const int e = e0 + q;
+        mf[q] = e < L ? lf[base + e] : T(1);
+        mh[q] = e < L ? lh[base + e] : T(1);
+    }
+    scan_multipliers<T, KPT, false>(mf, p0);
+    scan_multipliers<T, KPT, true>(mh, p1);
+    T *o = out + (size_t)(blockIdx.y * nlmax + line) * (14 * nthr);
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        o[k * nthr + tid] = p0[k];
+        o[(7 + k) * nthr + tid] = p1[k];
+    }
+}
+
+template <typename T>
+static int chain_pre_one(blp_handle *h, Coefs<T> &c) {
+    if (!chain2_applies(h, sizeof(T))) return BLP_OK;
+    const int nlmax = std::max(h->lay.R[2].mx, h->lay.R[1].my);
+    return with_chain_cfg<T>(h->L, [&](auto cfg) -> int {
+        using C = decltype(cfg);
+        const size_t n = (size_t)2 * nlmax * 14 * 32 * C::NW;
+        int rc;
+        void *p = nullptr, *q = nullptr;
+        if ((rc = blp_internal_alloc(h, &p, sizeof(T) * n))) return rc;
+        c.cpre = static_cast<T *>(p);
+        if ((rc = blp_internal_alloc(h, &q, sizeof(T) * n))) return rc;
+        c.cpreT = static_cast<T *>(q);
+        CUDA_TRY(cudaMemsetAsync(c.cpre, 0, sizeof(T) * n, h->stream));
+        CUDA_TRY(cudaMemsetAsync(c.cpreT, 0, sizeof(T) * n, h->stream));
+        const dim3 grid(std::max(nlmax, 1), 2);
+        k_chain_pre<T, C::KPT, C::NW, false><<<grid, 32 * C::NW, 0, h->stream>>>(h->lay, c.lf, c.lh, c.cpre, nlmax);
+        LAUNCH_CHECK(h);
+        k_chain_pre<T, C::KPT, C::NW, true><<<grid, 32 * C::NW, 0, h->stream>>>(h->lay, c.lfT, c.lhT, c.cpreT, nlmax);
+        LAUNCH_CHECK(h);
+        return BLP_OK;
+    });
+}
+
+int blp_internal_chain_pre(blp_handle *h) { return chain_pre_one<double>(h, h->cd); }
+
+// FP64 chains use the precomputed multipliers (the FP64 scans are bound by one
+// SM's FP64 FMA rate); FP32 chains, bound by latency, form them on the fly.
 template <typename T, int KPT, int NW, int NS, bool TRANS>
 static int launch_chain2(blp_handle *h, const ChainArgs<T> &a) {
-    constexpr size_t smem = NS * ChainSmem<T, KPT, NW>::stage;
-    static_assert(smem <= 200 * 1024, "line-chain stages exceed the shared-memory budget");
+    constexpr bool USEPRE = sizeof(T) == 8;
+    constexpr size_t smem = NS * ChainSmem<T, KPT, NW, USEPRE>::stage;
+    static_assert(smem <= 225 * 1024, "line-chain stages exceed the shared-memory budget");
     static std::atomic<bool> attr_set{false};
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_line_chain2<T, KPT, NW, NS, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024) != cudaSuccess) {
+        if (cudaFuncSetAttribute(k_line_chain2<T, KPT, NW, NS, TRANS, USEPRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 225 * 1024) != cudaSuccess) {
             cudaGetLastError();
             return BLP_ERR_CUDA;
         }
         attr_set = true;
     }
-    k_line_chain2<T, KPT, NW, NS, TRANS><<<2, 32 * NW, smem, h->stream>>>(a);
+    k_line_chain2<T, KPT, NW, NS, TRANS, USEPRE><<<2, 32 * NW, smem, h->stream>>>(a);
     LAUNCH_CHECK(h);
     return BLP_OK;
 }
@@ -840,24 +1010,18 @@ static int launch_chains(blp_handle *h, const Coefs<T> &c, const T *v, T *z, con
     a.lay = h->lay; a.v = v; a.z = z;
     a.wE = c.wE; a.wN = c.wN; a.wET = c.wET; a.wNT = c.wNT;
     a.lf = TRANS ? c.lfT : c.lf; a.lg = TRANS ? c.lgT : c.lg; a.lh = TRANS ? c.lhT : c.lh;
+    a.pre = nullptr; a.nlmax = 0;
     a.skip = skip;
     int L = h->L;
     // per line node: v, coupling, three factors, z = 6 words
     ProfScope ps(h, KC_LINE_CHAIN, (double)(h->lay.R[1].size + h->lay.R[2].size) * sizeof(T) * 6);
-    const bool aligned16 = (L * sizeof(T)) % 16 == 0 && (h->lay.R[1].off * sizeof(T)) % 16 == 0 &&
-                           (h->lay.R[2].off * sizeof(T)) % 16 == 0;
-    if (L <= 2048 && aligned16) {
-        // FP32: short FMA latency, so one warp per chain (longer thread
-        // segments, no CTA barrier); FP64: 4 warps to cut the sequential part
-        if constexpr (sizeof(T) == 4) {
-            if (L <= 512) return launch_chain2<T, 16, 1, 8, TRANS>(h, a);
-            if (L <= 1024) return launch_chain2<T, 16, 2, 6, TRANS>(h, a);
-            return launch_chain2<T, 16, 4, 3, TRANS>(h, a);
-        } else {
-            if (L <= 512) return launch_chain2<T, 4, 4, 6, TRANS>(h, a);
-            if (L <= 1024) return launch_chain2<T, 8, 4, 3, TRANS>(h, a);
-            return launch_chain2<T, 16, 4, 2, TRANS>(h, a);
-        }
+    if (chain2_applies(h, sizeof(T)) && (sizeof(T) == 4 || (TRANS ? c.cpreT : c.cpre))) {
+        a.pre = TRANS ? c.cpreT : c.cpre;
+        a.nlmax = std::max(h->lay.R[2].mx, h->lay.R[1].my);
+        return with_chain_cfg<T>(L, [&](auto cfg) -> int {
+            using C = decltype(cfg);
+            return launch_chain2<T, C::KPT, C::NW, C::NS, TRANS>(h, a);
+        });
     } else if (L <= 2048) {
         int nt = ((L + 3) / 4 + 31) / 32 * 32;
         k_line_chain<T, 4, TRANS><<<2, nt, 0, h->stream>>>(a);

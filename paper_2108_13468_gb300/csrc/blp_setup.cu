@@ -320,7 +320,8 @@ template <typename T>
 static void free_coefs(blp_handle *h, Coefs<T> &c) {
     blp_internal_free(h, c.pF);
     blp_internal_free(h, c.pR);
-    T *ps[] = {c.wW, c.wE, c.wS, c.wN, c.wET, c.wNT, c.wWT, c.wST, c.lf, c.lg, c.lh, c.lfT, c.lgT, c.lhT};
+    T *ps[] = {c.wW, c.wE, c.wS, c.wN, c.wET, c.wNT, c.wWT, c.wST, c.lf, c.lg, c.lh, c.lfT, c.lgT, c.lhT,
+               c.cpre, c.cpreT};
     for (T *p : ps) blp_internal_free(h, p);
     c = Coefs<T>();
 }
@@ -632,6 +633,7 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
                                                                 h->cd.lf, h->cd.lg, h->cd.lh, h->cd.lfT, h->cd.lgT, h->cd.lhT);
     LAUNCH_CHECK(h);
     TRY(convert_coefs(h, np));
+    TRY(blp_internal_chain_pre(h));
     TRY(build_hierarchy(h));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return BLP_OK;
