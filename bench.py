@@ -308,11 +308,11 @@ def measured_peak():
 
 
 def kernel_source_hash():
-    """Hash of the sources that define the preconditioner kernels (the
-    wavefront sweeps, the dominant class, among them)."""
+    """Hash of the sources that define the wavefront kernel (the dominant
+    class) and the shared definitions it includes."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2108_13468_gb300", "csrc")
-    for f in ("blp_common.cuh", "blp_precond.cu"):
+    for f in ("blp_common.cuh", "blp_dts.cuh"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

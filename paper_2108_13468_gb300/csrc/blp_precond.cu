@@ -15,509 +15,7 @@ namespace cg = cooperative_groups;
 
 #define FULL 0xffffffffu
 
-// ---------------------------------------------------------------------------
-// Wavefront kernel: downstream triangular solve on a SKEW block
-//     z(a,b) = beta(a,b) - cV(a,b) zV - cH(a,b) zH
-// forward (REV = false): zH = z(a+1,b) (east), zV = z(a,b+1) (north), the
-//   sweep starts at the top-right node (Sec. 3.1 M_II; Sec. 3.2 smoother);
-// reversed (REV = true): zH = z(a-1,b), zV = z(a,b-1), starting bottom-left
-//   (the transposed sweeps of the adjoint).
-// A Gauss-Seidel sweep of the full 5-point operator is this solve with
-// beta = b - (couplings to the neighbours that come later in the sweep) *
-// e_old, which k_gs_rhs forms in parallel beforehand; the result equals the
-// sequential sweep exactly because those neighbours still hold old values.
-//
-// Lane l of the warp that owns a 32-column strip handles column 32s+l and,
-// at step t, diagonal d = t (forward) or D-1-t (reversed), so each step
-// reads 32 consecutive words of beta and of the packed (cH, cV) pairs; those
-// arrive by bulk copies several chunks ahead, so memory latency stays off the
-// recurrence, whose step is one shuffle and two FMAs.  The lane next to the
-// previous strip ("head") takes that strip's boundary column from a ring in
-// shared memory filled by the warp that processed it.
-// All waits are bounded (BLP_ERR_TIMEOUT, no hang).
-// ---------------------------------------------------------------------------
-template <typename T> using Vec2T = Pair2<T>;
-
-#define DTS_RING 128
-
-template <typename T>
-struct DtsArgs {
-    Region R;
-    const T *beta;
-    const typename Vec2T<T>::type *pair;   // (cH, cV)
-    T *out;
-    const T *bnd;      // reversed interior sweep: global vector with the X/Y values west/south of the block
-    Layout lay;
-    const int *skip;   // nonzero -> return at once (converged)
-    int *err;
-};
-
-// --- bulk copies and mbarriers (inline PTX) --------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// global -> shared bulk copy (16-byte aligned, size a multiple of 16), completion on bar
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
-// bounded wait on the mbarrier phase of this warp's own bulk copies
-// (BLP_ERR_TIMEOUT instead of a hang).  It does not stop at the abort flag:
-// the copies read valid memory and always complete, and waiting for them
-// keeps any copy from landing after the CTA has exited.
-__device__ __forceinline__ void mbar_wait(unsigned long long *bar, unsigned parity, volatile unsigned *abort_flag, int *err) {
-    unsigned ready;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ready) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    if (ready) return;   // usually complete already
-    long long n = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if (++n > (BLP_SPIN_LIMIT >> 4)) {
-            *abort_flag = 1u;
-            atomicExch(err, BLP_ERR_TIMEOUT);
-            return;
-        }
-    }
-}
-
-// Shared-memory carve-up of one CTA: WC compute warps plus one copy warp.
-// Per compute warp: NST stages of CH diagonals of (cH, cV) pairs (T2) and
-// beta (T); an input ring of DTS_NSL slots of CH boundary values; full and
-// empty mbarriers per stage; one mbarrier per ring slot.  Then per compute
-// warp the count of ring slots its successor has released, the wave counter
-// and the abort flag.
-#define DTS_NSL 16
-
-template <typename T, int CH>
-struct DtsSmem {
-    typedef typename Vec2T<T>::type T2;
-    static constexpr size_t stage_pairs = (size_t)CH * 32 * sizeof(T2);
-    static constexpr size_t stage_beta = (size_t)CH * 32 * sizeof(T);
-    static constexpr size_t stage = stage_pairs + stage_beta;
-    static constexpr size_t ring = (size_t)DTS_NSL * CH * sizeof(T);
-    static size_t bytes(int WC, int NST) {
-        return (size_t)WC * (NST * stage + ring + 16 * (size_t)NST + 8 * DTS_NSL + 4) + 64;
-    }
-};
-
-// --- distributed shared memory and mbarrier helpers (inline PTX) -----------
-__device__ __forceinline__ unsigned mapa_u32(unsigned a, unsigned rank) {
-    unsigned r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-// CH boundary values into a (possibly peer) CTA's ring slot, as 16-byte
-// vector asynchronous stores whose bytes complete the transaction count of
-// that slot's mbarrier
-template <int CH>
-__device__ __forceinline__ void st_async_slot(unsigned addr, const float (&v)[CH], unsigned bar) {
-#pragma unroll
-    for (int i = 0; i < CH / 4; i++)
-        asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];\n"
-                     ::"r"(addr + 16 * i), "r"(__float_as_uint(v[4 * i])), "r"(__float_as_uint(v[4 * i + 1])),
-                     "r"(__float_as_uint(v[4 * i + 2])), "r"(__float_as_uint(v[4 * i + 3])), "r"(bar) : "memory");
-}
-template <int CH>
-__device__ __forceinline__ void st_async_slot(unsigned addr, const double (&v)[CH], unsigned bar) {
-#pragma unroll
-    for (int i = 0; i < CH / 2; i++)
-        asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];\n"
-                     ::"r"(addr + 16 * i), "l"(__double_as_longlong(v[2 * i])), "l"(__double_as_longlong(v[2 * i + 1])),
-                     "r"(bar) : "memory");
-}
-__device__ __forceinline__ void st_relaxed_cluster(unsigned addr, unsigned v) {
-    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_cluster(unsigned addr, unsigned v) {
-    asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire_cluster(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32(p)) : "memory");
-    return v;
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// bounded wait for a ring slot filled by a peer (stops at the abort flag)
-__device__ __forceinline__ bool mbar_test_wait_cluster(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void mbar_wait_cluster(unsigned long long *bar, unsigned parity, volatile unsigned *abort_flag,
-                                                  int *err, long long limit = BLP_SPIN_LIMIT >> 4) {
-    if (mbar_test_wait_cluster(bar, parity)) return;   // usually complete already
-    long long n = 0;
-    while (!mbar_try_wait_cluster(bar, parity)) {
-        if (*abort_flag) return;
-        if (++n > limit) {
-            *abort_flag = 1u;
-            atomicExch(err, BLP_ERR_TIMEOUT);
-            return;
-        }
-    }
-}
-// bounded wait until the local counter *ctr (written by a peer) >= target
-__device__ __forceinline__ void wait_counter(const unsigned *ctr, int target, volatile unsigned *abort_flag, int *err,
-                                             long long limit = BLP_SPIN_LIMIT) {
-    long long n = 0;
-    while ((int)ld_acquire_cluster(ctr) < target) {
-        if (*abort_flag) return;
-        if (++n > limit) {
-            *abort_flag = 1u;
-            atomicExch(err, BLP_ERR_TIMEOUT);
-            return;
-        }
-    }
-}
-
-// The kernel runs as one thread-block cluster of CL CTAs, each with WC
-// compute warps and one copy warp (W = CL*WC compute warps; global compute
-// warp g = rank*WC + w).  Strips go to compute warps in waves of W.
-//  - The copy warp keeps NST stages per compute warp filled with bulk
-//    copies (full / empty mbarriers), so compute warps never issue copies.
-//  - Inside a wave the boundary column passes from warp g to warp g+1 (same
-//    CTA or the next CTA): chunk j of the producer (its CH tail-lane values)
-//    goes by two vector asynchronous stores into slot j of g+1's ring, whose
-//    mbarrier the stores complete; consumer chunk c reads slots c+3 and
-//    c+4 (the 31-row skew between neighbouring strips), and a relaxed
-//    counter of released slots keeps the producer from overwriting early.
-//  - Between waves the last strip's boundary column goes through global
-//    memory, announced by a counter in CTA 0 (release / acquire).
-// Spreading the strips over CL SMs multiplies the bandwidth that feeds the
-// recurrences.  All waits are bounded.
-template <typename T, bool REV, int CH, bool BND>
-__global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
-    static_assert(CH == 8 || CH == 16, "ring slots carry 8 or 16 values");
-    constexpr int SK = 31 / CH;   // the 31-row skew spans SK whole chunks
-    typedef typename Vec2T<T>::type T2;
-    typedef DtsSmem<T, CH> SM;
-    if (A.skip && *A.skip) return;   // same value in every CTA of the cluster
-    cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int WC = (blockDim.x >> 5) - 1, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
-    const int W = CL * WC;
-    unsigned char *const stages = smem_raw;
-    unsigned char *const rings = stages + (size_t)WC * NST * SM::stage;
-    unsigned long long *const fullb = reinterpret_cast<unsigned long long *>(rings + (size_t)WC * SM::ring);
-    unsigned long long *const emptyb = fullb + (size_t)WC * NST;
-    unsigned long long *const rbars = emptyb + (size_t)WC * NST;
-    unsigned *const relc = reinterpret_cast<unsigned *>(rbars + (size_t)WC * DTS_NSL);
-    unsigned *const wave_done = relc + WC;
-    volatile unsigned *const abort_flag = wave_done + 1;
-
-    const Region R = A.R;
-    const int S = R.S, D = R.D, my = R.my;
-    const int qoff = REV ? D - (my + 31) : 0;   // padding diagonals come first in reversed order
-    const int head = REV ? 0 : 31, tail = REV ? 31 : 0;
-    const int nch = D / CH;
-
-    if (threadIdx.x < WC) relc[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) { *wave_done = 0u; *abort_flag = 0u; }
-    if (w < WC && lane == 0) {
-        for (int q = 0; q < NST; q++) {
-            mbar_init(fullb + w * NST + q, 1);
-            mbar_init(emptyb + w * NST + q, 1);
-        }
-        for (int q = 0; q < DTS_NSL; q++) mbar_init(rbars + w * DTS_NSL + q, 1);
-        for (int q = 0; q < DTS_NSL; q++) mbar_arrive_expect_tx(rbars + w * DTS_NSL + q, (unsigned)(CH * sizeof(T)));
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    cluster.sync();   // every CTA initialised before any peer writes into it
-
-    if (w == WC) {
-        // ---- copy warp: lane 0 fills the stages of every compute warp ----
-        if (lane == 0) {
-            int kk[16], cc[16], seq[16];
-            for (int i = 0; i < WC; i++) { kk[i] = 0; cc[i] = 0; seq[i] = 0; }
-            int left = 0;
-            for (int i = 0; i < WC; i++) left += (rank * WC + i < S) ? 1 : 0;
-            long long n = 0;
-            while (left > 0) {
-                bool any = false;
-                for (int i = 0; i < WC; i++) {
-                    const int gi = rank * WC + i;
-                    const int sidx = gi + kk[i] * W;
-                    if (sidx >= S) continue;
-                    const int q = seq[i] % NST, use = seq[i] / NST;
-                    if (use > 0 && !mbar_test_wait(emptyb + i * NST + q, (unsigned)(use - 1) & 1u)) continue;
-                    const int s = REV ? sidx : S - 1 - sidx;
-                    const long long sbase = R.off + (((long long)s * D) << 5);
-                    const int c = cc[i];
-                    const int d0 = REV ? D - (c + 1) * CH : c * CH;
-                    unsigned char *st = stages + ((size_t)i * NST + q) * SM::stage;
-                    mbar_arrive_expect_tx(fullb + i * NST + q, (unsigned)SM::stage);
-                    bulk_g2s(st, A.pair + sbase + ((long long)d0 << 5), (unsigned)SM::stage_pairs, fullb + i * NST + q);
-                    bulk_g2s(st + SM::stage_pairs, A.beta + sbase + ((long long)d0 << 5), (unsigned)SM::stage_beta,
-                             fullb + i * NST + q);
-                    seq[i]++;
-                    if (++cc[i] == nch) {
-                        cc[i] = 0;
-                        kk[i]++;
-                        if (gi + kk[i] * W >= S) left--;
-                    }
-                    any = true;
-                }
-                if (!any && ++n > BLP_SPIN_LIMIT) {   // compute warps stopped consuming
-                    *abort_flag = 1u;
-                    atomicExch(A.err, BLP_ERR_TIMEOUT);
-                    break;
-                }
-            }
-        }
-        __syncwarp();
-        cluster.sync();
-        return;
-    }
-
-    // ---- compute warps ----
-    const int g = rank * WC + w;
-    unsigned char *const mystage = stages + (size_t)w * NST * SM::stage;
-    unsigned long long *const myfull = fullb + (size_t)w * NST;
-    unsigned long long *const myempty = emptyb + (size_t)w * NST;
-    unsigned long long *const myrbar = rbars + (size_t)w * DTS_NSL;
-    const T *const ring_w = reinterpret_cast<const T *>(rings + (size_t)w * SM::ring);
-    // successor g+1 (its ring and ring mbarriers), predecessor g-1 (its
-    // released-slot counter), CTA 0's wave counter: shared::cluster addresses
-    const int sg = g + 1 < W ? g + 1 : g, pg = g > 0 ? g - 1 : g;
-    const unsigned succ_ring = mapa_u32(smem_u32(rings) + (unsigned)((sg % WC) * SM::ring), (unsigned)(sg / WC));
-    const unsigned succ_rbar = mapa_u32(smem_u32(rbars) + (unsigned)((sg % WC) * DTS_NSL * 8), (unsigned)(sg / WC));
-    const unsigned pred_rel = mapa_u32(smem_u32(relc) + (unsigned)((pg % WC) * 4), (unsigned)(pg / WC));
-    const unsigned wave_cta0 = mapa_u32(smem_u32(wave_done), 0u);
-
-    int k_in = 0, k_out = 0;   // strips consumed from g-1 / produced for g+1
-    int seq = 0;               // chunks taken from the stages
-
-    for (int k = 0;; k++) {
-        const int sidx = g + k * W;
-        if (sidx >= S) break;
-        const int s = REV ? sidx : S - 1 - sidx;
-        const bool has_in = g > 0;
-        const bool from_global = g == 0 && sidx > 0;
-        const bool has_out = (g + 1 < W) && (sidx + 1 < S);
-        const int sprev = REV ? s - 1 : s + 1;
-        const long long sbase = R.off + (((long long)s * D) << 5);
-        if (from_global) wait_counter(wave_done, k, abort_flag, A.err);   // g == 0 lives in CTA 0
-        int waited = 0, released = 0;   // ring slots of this strip waited for / released
-        T zprev = T(0);
-        T *const outp = A.out + sbase + lane;
-        for (int c = 0; c < nch; c++) {
-            const int t0 = c * CH;
-            T hz[CH];
-#pragma unroll
-            for (int u = 0; u < CH; u++) hz[u] = T(0);
-            if (from_global) {
-#pragma unroll
-                for (int u = 0; u < CH; u++) {
-                    const int t = t0 + u;
-                    const int ktop = REV ? D - 1 - t - 31 : t;
-                    const int dprev = REV ? ktop : ktop + 31;
-                    if (lane == head && ktop >= 0 && ktop < my)
-                        hz[u] = __ldcg(A.out + R.off + (((long long)sprev * D + dprev) << 5) + (REV ? 31 : 0));
-                }
-            }
-            if (has_in) {
-                const int upto = min(c + SK + 1, nch - 1);
-                for (; waited <= upto; waited++) {
-                    const int P = k_in * nch + waited;
-                    mbar_wait_cluster(myrbar + P % DTS_NSL, (unsigned)(P / DTS_NSL) & 1u, abort_flag, A.err);
-                }
-                // row t0+u-qoff left the producer at its step t0+u+31: slot
-                // c + (u+31)/CH, value (u+31) % CH, i.e. the last value of slot
-                // c+SK (u = 0) or value u-1 of slot c+SK+1 (u >= 1)
-                const int Pa = k_in * nch + c + SK, Pb = Pa + 1;
-                const T *sa = ring_w + (Pa % DTS_NSL) * CH, *sb = ring_w + (Pb % DTS_NSL) * CH;
-#pragma unroll
-                for (int u = 0; u < CH; u++) {
-                    const int row = t0 + u - qoff;
-                    const T v = u == 0 ? sa[CH - 1] : sb[u - 1];
-                    hz[u] = (row >= 0 && row < my) ? v : T(0);
-                }
-            }
-            const int q = seq % NST;
-            mbar_wait(myfull + q, (unsigned)(seq / NST) & 1u, abort_flag, A.err);
-            const T2 *const pp = reinterpret_cast<const T2 *>(mystage + (size_t)q * SM::stage);
-            const T *const pb = reinterpret_cast<const T *>(mystage + (size_t)q * SM::stage + SM::stage_pairs);
-            const bool is_head = lane == head;
-            T *const op = outp + ((long long)(REV ? D - 1 - t0 : t0) << 5);
-            T tz[CH];
-#pragma unroll
-            for (int u = 0; u < CH; u++) {
-                const int ui = REV ? CH - 1 - u : u;
-                const T2 cpair = pp[ui * 32 + lane];
-                const T beta = pb[ui * 32 + lane];
-                T zH = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
-                zH = is_head ? hz[u] : zH;
-                T zV = zprev;
-                if (BND) {   // reversed interior sweep: west / south neighbours in the X / Y blocks
-                    const int ktop = (REV ? D - 1 - (t0 + u) : t0 + u) - 31 + lane;
-                    const int a = s * 32 + lane, b = my - 1 - ktop;
-                    if (ktop >= 0 && ktop < my && a < R.mx) {
-                        if (a == 0) zH = A.bnd[A.lay.addr(R.i0 - 1, R.j0 + b)];
-                        if (b == 0) zV = A.bnd[A.lay.addr(R.i0 + a, R.j0 - 1)];
-                    }
-                }
-                T z = beta - cpair.y * zV;
-                z = z - cpair.x * zH;
-                op[REV ? -(u << 5) : (u << 5)] = z;
-                tz[u] = z;
-                zprev = z;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(myempty + q);   // stage read: the copy warp may refill it
-            seq++;
-            if (has_out) {
-                const int P = k_out * nch + c;   // slot sequence number in the successor's ring
-                wait_counter(relc + w, P - DTS_NSL + 1, abort_flag, A.err);
-                if (lane == tail)
-                    st_async_slot<CH>(succ_ring + (unsigned)((P % DTS_NSL) * CH * sizeof(T)), tz,
-                                  succ_rbar + (unsigned)((P % DTS_NSL) * 8));
-            }
-            if (has_in && lane == head && !*abort_flag) {
-                // slots no later chunk reads: re-arm for their next use, release
-                const int rel = c == nch - 1 ? nch : min(c + SK + 1, nch);
-                for (; released < rel; released++) {
-                    const int P = k_in * nch + released;
-                    mbar_arrive_expect_tx(myrbar + P % DTS_NSL, (unsigned)(CH * sizeof(T)));
-                }
-                st_relaxed_cluster(pred_rel, (unsigned)(k_in * nch + released));
-            }
-            __syncwarp();
-        }
-        if (has_in) k_in++;
-        if (has_out) k_out++;
-        // the next wave's first warp reads this strip's boundary column from global memory
-        if (g == W - 1 && sidx + 1 < S && lane == tail) st_release_cluster(wave_cta0, (unsigned)(k + 1));
-    }
-    __syncwarp();
-    cluster.sync();
-}
-
-// Self-check of the bounded waits: one warp waits, with the kernels' own
-// helpers and a short iteration limit, for a counter and an mbarrier phase
-// that nothing completes.  Each wait must give up, record BLP_ERR_TIMEOUT
-// and return; err[0] / err[1] receive the two outcomes.
-__global__ void k_wait_probe(int *err, long long limit) {
-    __shared__ unsigned ctr;
-    __shared__ unsigned abort_flag;
-    __shared__ __align__(8) unsigned long long bar;
-    if (threadIdx.x == 0) {
-        ctr = 0u;
-        abort_flag = 0u;
-        mbar_init(&bar, 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    __syncthreads();
-    wait_counter(&ctr, 1, &abort_flag, err, limit);
-    __syncwarp();
-    if (threadIdx.x == 0) abort_flag = 0u;
-    __syncwarp();
-    mbar_wait_cluster(&bar, 0u, &abort_flag, err + 1, limit);
-}
-
-extern "C" int blp_check_wait_timeout(blp_handle *h) {
-    if (!h) return BLP_ERR_ARG;
-    int res[2] = {0, 0};
-    CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
-    k_wait_probe<<<1, 32, 0, h->stream>>>(h->err, 2000);
-    LAUNCH_CHECK(h);
-    CUDA_TRY(cudaMemcpyAsync(res, h->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return (res[0] == BLP_ERR_TIMEOUT && res[1] == BLP_ERR_TIMEOUT) ? BLP_ERR_TIMEOUT : BLP_OK;
-}
-
-// Cluster shape for a block of S strips: CL <= max_cluster CTAs (one per
-// SM: the dynamic shared memory is padded so that two CTAs cannot share an
-// SM) of WC <= 15 compute warps, and as many bulk-copy stages as fit.
-struct DtsShape { int CL, WC, NST; size_t smem; };
-template <typename T, int CH>
-static DtsShape dts_shape(int S, int max_cluster) {
-    typedef DtsSmem<T, CH> SM;
-    const size_t cap = 225 * 1024;
-    DtsShape sh;
-    sh.CL = std::max(1, std::min(max_cluster, S));
-    sh.WC = std::min(15, (S + sh.CL - 1) / sh.CL);
-    sh.CL = std::min(sh.CL, (S + sh.WC - 1) / sh.WC);
-    sh.NST = 16;
-    while (sh.NST > 2 && SM::bytes(sh.WC, sh.NST) > cap) sh.NST--;
-    sh.smem = SM::bytes(sh.WC, sh.NST);
-    if (sh.CL > 1) sh.smem = std::max(sh.smem, (size_t)120 * 1024);
-    return sh;
-}
-
-template <typename T, bool REV, int CH>
-static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls) {
-    static std::atomic<bool> attr_set{false};
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(k_dts<T, REV, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess ||
-            cudaFuncSetAttribute(k_dts<T, REV, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess) {
-            cudaGetLastError();
-            return BLP_ERR_CUDA;
-        }
-        attr_set = true;
-    }
-    const DtsShape sh = dts_shape<T, CH>(a.R.S, h->dts_max_cluster);
-    if (DtsSmem<T, CH>::bytes(sh.WC, sh.NST) > 225 * 1024) return BLP_ERR_ARG;
-    // algorithmic words per node: beta, two couplings, out
-    ProfScope ps(h, cls, (double)a.R.mx * a.R.my * sizeof(T) * 4);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = sh.CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(sh.CL);
-    cfg.blockDim = dim3((sh.WC + 1) * 32);
-    cfg.dynamicSmemBytes = sh.smem;
-    cfg.stream = h->stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = a.bnd ? cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, true>, a, sh.NST)
-                          : cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, false>, a, sh.NST);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return BLP_ERR_CUDA;
-    }
-    LAUNCH_CHECK(h);
-    return BLP_OK;
-}
-
-// Chunk length: 16 diagonals amortise the per-chunk synchronisation; 8
-// halves the hand-off lag.
-template <typename T, bool REV>
-static int launch_dts(blp_handle *h, const DtsArgs<T> &a, int cls) {
-    return h->dts_chunk == 8 ? launch_dts_ch<T, REV, 8>(h, a, cls) : launch_dts_ch<T, REV, 16>(h, a, cls);
-}
+#include "blp_dts.cuh"
 
 // Right-hand side of one Gauss-Seidel sweep in the wavefront form:
 //   forward  beta = b - wW e_old(a-1,b) - wS e_old(a,b-1)
