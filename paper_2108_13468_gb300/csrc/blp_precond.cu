@@ -792,8 +792,8 @@ __global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
     if (A.skip && *A.skip) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[8];
-    CLev<T> LV[BLP_MAXLEV];
-    {
+    __shared__ CLev<T> LV[BLP_MAXLEV];   // level descriptors (one copy, not per thread)
+    if (threadIdx.x == 0) {
         T *p = reinterpret_cast<T *>(smem_raw);
         for (int l = A.l0; l < A.nlev; l++) {
             const int m = A.m[l], n = m * m;
@@ -804,23 +804,56 @@ __global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
             L.cw = p; p += n; L.ce = p; p += n; L.cs = p; p += n; L.cn = p; p += n; L.om = p; p += n;
             L.wt = TRANS ? p : L.om;
             if (TRANS) p += n;
-            const T *nat = A.nat[l];
+        }
+    }
+    __syncthreads();
+    {
+        for (int l = A.l0; l < A.nlev; l++) {
+            const int n = A.m[l] * A.m[l];
+            const CLev<T> L = LV[l];
+            const T *__restrict__ nat = A.nat[l];
             const int q0 = TRANS ? 4 : 0;
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                L.cw[k] = nat[(long long)(q0 + 0) * n + k];
-                L.ce[k] = nat[(long long)(q0 + 1) * n + k];
-                L.cs[k] = nat[(long long)(q0 + 2) * n + k];
-                L.cn[k] = nat[(long long)(q0 + 3) * n + k];
-                L.om[k] = nat[(long long)8 * n + k];
-                if (TRANS) L.wt[k] = nat[(long long)9 * n + k];
+            // four elements per thread in flight: the loads are issued before the stores
+            for (int k0 = threadIdx.x; k0 < n; k0 += 4 * blockDim.x) {
+                T v[4][6];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int k = k0 + u * blockDim.x;
+                    if (k < n) {
+                        v[u][0] = __ldg(nat + (long long)(q0 + 0) * n + k);
+                        v[u][1] = __ldg(nat + (long long)(q0 + 1) * n + k);
+                        v[u][2] = __ldg(nat + (long long)(q0 + 2) * n + k);
+                        v[u][3] = __ldg(nat + (long long)(q0 + 3) * n + k);
+                        v[u][4] = __ldg(nat + (long long)8 * n + k);
+                        v[u][5] = TRANS ? __ldg(nat + (long long)9 * n + k) : T(0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int k = k0 + u * blockDim.x;
+                    if (k < n) {
+                        L.cw[k] = v[u][0]; L.ce[k] = v[u][1]; L.cs[k] = v[u][2]; L.cn[k] = v[u][3];
+                        L.om[k] = v[u][4];
+                        if (TRANS) L.wt[k] = v[u][5];
+                    }
+                }
             }
         }
     }
     const int l0 = A.l0, last = A.nlev - 1, m0 = A.m[l0];
     const Region R0 = A.R0;
-    for (int k = threadIdx.x; k < m0 * m0; k += blockDim.x) {
-        LV[l0].b[k] = A.b_in[R0.addr(k % m0, k / m0)];
-        LV[l0].e[k] = T(0);
+    for (int k0 = threadIdx.x; k0 < m0 * m0; k0 += 4 * blockDim.x) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int k = k0 + u * blockDim.x;
+            if (k < m0 * m0) v[u] = __ldg(A.b_in + R0.addr(k % m0, k / m0));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int k = k0 + u * blockDim.x;
+            if (k < m0 * m0) { LV[l0].b[k] = v[u]; LV[l0].e[k] = T(0); }
+        }
     }
     __syncthreads();
 
