@@ -235,7 +235,7 @@ struct blp_handle {
     cudaStream_t stream = 0;
     long long launches = 0;
     int dts_max_cluster = 8;        // CTAs per wavefront cluster (1..8)
-    int dts_chunk = 16;             // wavefront chunk length (8 or 16 diagonals)
+    int dts_chunk = 0;              // wavefront chunk length (8, 16, 32 diagonals; 0: by precision)
     double t_setup_ms = 0.0;
     int last_cycles = 0;
     // Krylov work space (allocated lazily)

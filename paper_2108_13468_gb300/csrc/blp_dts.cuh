@@ -214,7 +214,7 @@ __device__ __forceinline__ void wait_counter(const unsigned *ctr, int target, vo
 // recurrences.  All waits are bounded.
 template <typename T, bool REV, int CH, bool BND>
 __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
-    static_assert(CH == 8 || CH == 16, "ring slots carry 8 or 16 values");
+    static_assert(CH == 8 || CH == 16 || CH == 32, "ring slots carry 8, 16 or 32 values");
     constexpr int SK = 31 / CH;   // the 31-row skew spans SK whole chunks
     typedef typename Vec2T<T>::type T2;
     typedef DtsSmem<T, CH> SM;
@@ -473,6 +473,12 @@ static DtsShape dts_shape(int S, int max_cluster) {
     return sh;
 }
 
+template <typename T, int CH>
+static bool dts_fits(int S, int max_cluster, int min_stages) {
+    const DtsShape sh = dts_shape<T, CH>(S, max_cluster);
+    return sh.NST >= min_stages && DtsSmem<T, CH>::bytes(sh.WC, sh.NST) <= 225 * 1024;
+}
+
 template <typename T, bool REV, int CH>
 static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls) {
     static std::atomic<bool> attr_set{false};
@@ -510,10 +516,18 @@ static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls) {
     return BLP_OK;
 }
 
-// Chunk length: 16 diagonals amortise the per-chunk synchronisation; 8
-// halves the hand-off lag.
 template <typename T, bool REV>
 static int launch_dts(blp_handle *h, const DtsArgs<T> &a, int cls) {
-    return h->dts_chunk == 8 ? launch_dts_ch<T, REV, 8>(h, a, cls) : launch_dts_ch<T, REV, 16>(h, a, cls);
+    // default: 32 rows in FP32 (the per-chunk hand-off dominates a 38-cycle
+    // step), 16 in FP64 (a 220-cycle step dominates; shorter lag)
+    // shorter chunks where the cluster shape's stages would not fit (many
+    // warps per CTA on the largest blocks); the 32-row chunk only with at
+    // least 4 stages of prefetch
+    int ch = h->dts_chunk ? h->dts_chunk : (sizeof(T) == 4 ? 32 : 16);
+    if (ch == 32 && !dts_fits<T, 32>(a.R.S, h->dts_max_cluster, 4)) ch = 16;
+    if (ch == 16 && !dts_fits<T, 16>(a.R.S, h->dts_max_cluster, 2)) ch = 8;
+    if (ch == 8) return launch_dts_ch<T, REV, 8>(h, a, cls);
+    if (ch == 32) return launch_dts_ch<T, REV, 32>(h, a, cls);
+    return launch_dts_ch<T, REV, 16>(h, a, cls);
 }
 

@@ -654,7 +654,10 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
     h->p = *p;
     // tuning override: CTAs per wavefront cluster (1 = single-SM wavefront)
     if (const char *e = getenv("BLP_DTS_CLUSTER")) h->dts_max_cluster = std::max(1, std::min(8, atoi(e)));
-    if (const char *e = getenv("BLP_DTS_CHUNK")) h->dts_chunk = atoi(e) == 8 ? 8 : 16;
+    if (const char *e = getenv("BLP_DTS_CHUNK")) {
+        const int c = atoi(e);
+        h->dts_chunk = (c == 8 || c == 16 || c == 32) ? c : 0;
+    }
     if (const char *e = getenv("BLP_GRAPHS")) h->use_graphs = atoi(e) != 0;
     h->stream = stream;
     int rc = setup_impl(h, c1, c2, r);

@@ -90,10 +90,11 @@ def test_large_mesh_n2048_against_oracle_fgmres():
         s.close()
 
 
-def test_large_mesh_n4096_residual_and_error_bound():
+@pytest.mark.parametrize("precision", [blp.BLP_MIXED, blp.BLP_FP64])
+def test_large_mesh_n4096_residual_and_error_bound(precision):
     N, eps = 4096, 1e-6
     p = large_problem(N, eps)
-    s = blp.Solver(N, eps, T(p.c1), T(p.c2), T(p.r), precision=blp.BLP_MIXED, maxit=500)
+    s = blp.Solver(N, eps, T(p.c1), T(p.c2), T(p.r), precision=precision, maxit=500)
     u, info = s.solve(T(p.f), tol=1e-11)   # tighter: the max-norm bound is the only error guarantee here
     assert info.status == 0 and info.relres <= 1e-11
     assert residual_checks(N, eps, p, u, tol=1e-11) < 1e-4
