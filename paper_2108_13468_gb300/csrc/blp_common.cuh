@@ -234,7 +234,9 @@ struct blp_handle {
     int *err = nullptr;             // device error word (timeouts)
     cudaStream_t stream = 0;
     long long launches = 0;
-    int dts_max_cluster = 8;        // CTAs per wavefront cluster (1..8)
+    int dts_max_cluster = 8;        // CTAs per wavefront cluster (1..16)
+    bool dts_two_step32 = true;     // two-step form of the wavefront recurrence, FP32 sweeps
+    bool dts_two_step64 = false;    // FP64: off (its extra DFMAs cost more than the shorter chain saves)
     int dts_chunk = 0;              // wavefront chunk length (8, 16, 32 diagonals; 0: by precision)
     double t_setup_ms = 0.0;
     int last_cycles = 0;

@@ -212,9 +212,23 @@ __device__ __forceinline__ void wait_counter(const unsigned *ctr, int target, vo
 //    memory, announced by a counter in CTA 0 (release / acquire).
 // Spreading the strips over CL SMs multiplies the bandwidth that feeds the
 // recurrences.  All waits are bounded.
-template <typename T, bool REV, int CH, bool BND>
+//
+// LA (two-step form): substituting the recurrence into itself once gives,
+// for step t+1 of lane l with n = the upstream lane (l+1 forward, l-1
+// reversed),
+//     z_{t+1}(l) = K + A z_{t-1}(l) + B z_{t-1}(n) + C z_{t-1}(n'),  n' = n's upstream lane,
+//     K = beta_{t+1} - cV_{t+1} beta_t(l) - cH_{t+1} beta_t(n),
+//     A = cV_{t+1} cV_t(l),  B = cV_{t+1} cH_t(l) + cH_{t+1} cV_t(n),  C = cH_{t+1} cH_t(n),
+// so the dependency chain advances two steps per three FMAs instead of four;
+// z_t(l) itself is formed beside it, off the chain.  The head lane's
+// upstream value z_t(n) is the boundary value it receives, so it takes
+// n's coefficients as zero and n's beta as that value; the lane next to it
+// takes its z_{t-1}(n') from the boundary as well.  Same arithmetic as the
+// sequential sweep up to rounding order.
+template <typename T, bool REV, int CH, bool BND, bool LA>
 __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
     static_assert(CH == 8 || CH == 16 || CH == 32, "ring slots carry 8, 16 or 32 values");
+    static_assert(!(LA && BND), "the two-step form has no boundary-vector variant");
     constexpr int SK = 31 / CH;   // the 31-row skew spans SK whole chunks
     typedef typename Vec2T<T>::type T2;
     typedef DtsSmem<T, CH> SM;
@@ -339,7 +353,7 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
                     const int t = t0 + u;
                     const int ktop = REV ? D - 1 - t - 31 : t;
                     const int dprev = REV ? ktop : ktop + 31;
-                    if (lane == head && ktop >= 0 && ktop < my)
+                    if ((LA || lane == head) && ktop >= 0 && ktop < my)
                         hz[u] = __ldcg(A.out + R.off + (((long long)sprev * D + dprev) << 5) + (REV ? 31 : 0));
                 }
             }
@@ -368,6 +382,35 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
             const bool is_head = lane == head;
             T *const op = outp + ((long long)(REV ? D - 1 - t0 : t0) << 5);
             T tz[CH];
+            if constexpr (LA) {
+                const bool next_head = lane == (REV ? 1 : 30);
+                const int nl = REV ? max(lane - 1, 0) : min(lane + 1, 31);   // upstream lane (clamped)
+#pragma unroll
+                for (int u = 0; u < CH; u += 2) {
+                    const int ui0 = REV ? CH - 1 - u : u, ui1 = REV ? CH - 2 - u : u + 1;
+                    const T2 c0 = pp[ui0 * 32 + lane], c1 = pp[ui1 * 32 + lane];
+                    const T b0 = pb[ui0 * 32 + lane], b1 = pb[ui1 * 32 + lane];
+                    T2 n0 = pp[ui0 * 32 + nl];
+                    T nb0 = pb[ui0 * 32 + nl];
+                    if (is_head) { n0.x = T(0); n0.y = T(0); nb0 = hz[u + 1]; }
+                    const T K = b1 - c1.y * b0 - c1.x * nb0;
+                    const T Ac = c1.y * c0.y, Bc = c1.y * c0.x + c1.x * n0.y, Cc = c1.x * n0.x;
+                    T Z1 = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
+                    T Z2 = REV ? __shfl_up_sync(FULL, zprev, 2) : __shfl_down_sync(FULL, zprev, 2);
+                    Z1 = is_head ? hz[u] : Z1;
+                    Z2 = is_head ? T(0) : (next_head ? hz[u] : Z2);
+                    T z1 = K + Ac * zprev;
+                    z1 = z1 + Bc * Z1;
+                    z1 = z1 + Cc * Z2;
+                    T z0 = b0 - c0.y * zprev;
+                    z0 = z0 - c0.x * Z1;
+                    op[REV ? -(u << 5) : (u << 5)] = z0;
+                    op[REV ? -((u + 1) << 5) : ((u + 1) << 5)] = z1;
+                    tz[u] = z0;
+                    tz[u + 1] = z1;
+                    zprev = z1;
+                }
+            } else {
 #pragma unroll
             for (int u = 0; u < CH; u++) {
                 const int ui = REV ? CH - 1 - u : u;
@@ -389,6 +432,7 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
                 op[REV ? -(u << 5) : (u << 5)] = z;
                 tz[u] = z;
                 zprev = z;
+            }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(myempty + q);   // stage read: the copy warp may refill it
@@ -479,15 +523,25 @@ static bool dts_fits(int S, int max_cluster, int min_stages) {
     return sh.NST >= min_stages && DtsSmem<T, CH>::bytes(sh.WC, sh.NST) <= 225 * 1024;
 }
 
+template <typename K>
+static bool dts_attrs(K kern) {
+    // clusters above 8 CTAs are non-portable and must be allowed per kernel
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <typename T, bool REV, int CH>
-static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls) {
+static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls, bool la) {
+    constexpr bool HAS_LA = CH >= 16;   // the 8-row fallback keeps the one-step form
     static std::atomic<bool> attr_set{false};
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_dts<T, REV, CH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess ||
-            cudaFuncSetAttribute(k_dts<T, REV, CH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess) {
-            cudaGetLastError();
+        if (!dts_attrs(k_dts<T, REV, CH, false, false>) || !dts_attrs(k_dts<T, REV, CH, true, false>) ||
+            (HAS_LA && !dts_attrs(k_dts<T, REV, CH, false, HAS_LA>)))
             return BLP_ERR_CUDA;
-        }
         attr_set = true;
     }
     const DtsShape sh = dts_shape<T, CH>(a.R.S, h->dts_max_cluster);
@@ -506,8 +560,9 @@ static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls) {
     cfg.stream = h->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = a.bnd ? cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, true>, a, sh.NST)
-                          : cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, false>, a, sh.NST);
+    cudaError_t e = a.bnd             ? cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, true, false>, a, sh.NST)
+                    : (HAS_LA && la) ? cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, false, HAS_LA>, a, sh.NST)
+                                     : cudaLaunchKernelEx(&cfg, k_dts<T, REV, CH, false, false>, a, sh.NST);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return BLP_ERR_CUDA;
@@ -526,8 +581,9 @@ static int launch_dts(blp_handle *h, const DtsArgs<T> &a, int cls) {
     int ch = h->dts_chunk ? h->dts_chunk : (sizeof(T) == 4 ? 32 : 16);
     if (ch == 32 && !dts_fits<T, 32>(a.R.S, h->dts_max_cluster, 4)) ch = 16;
     if (ch == 16 && !dts_fits<T, 16>(a.R.S, h->dts_max_cluster, 2)) ch = 8;
-    if (ch == 8) return launch_dts_ch<T, REV, 8>(h, a, cls);
-    if (ch == 32) return launch_dts_ch<T, REV, 32>(h, a, cls);
-    return launch_dts_ch<T, REV, 16>(h, a, cls);
+    const bool la = sizeof(T) == 4 ? h->dts_two_step32 : h->dts_two_step64;
+    if (ch == 8) return launch_dts_ch<T, REV, 8>(h, a, cls, la);
+    if (ch == 32) return launch_dts_ch<T, REV, 32>(h, a, cls, la);
+    return launch_dts_ch<T, REV, 16>(h, a, cls, la);
 }
 

@@ -653,7 +653,12 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
     blp_handle *h = new blp_handle();
     h->p = *p;
     // tuning override: CTAs per wavefront cluster (1 = single-SM wavefront)
-    if (const char *e = getenv("BLP_DTS_CLUSTER")) h->dts_max_cluster = std::max(1, std::min(8, atoi(e)));
+    if (const char *e = getenv("BLP_DTS_CLUSTER")) h->dts_max_cluster = std::max(1, std::min(16, atoi(e)));
+    if (const char *e = getenv("BLP_DTS_TWO_STEP")) {   // bit 0: FP32 sweeps, bit 1: FP64 sweeps
+        const int v = atoi(e);
+        h->dts_two_step32 = (v & 1) != 0;
+        h->dts_two_step64 = (v & 2) != 0;
+    }
     if (const char *e = getenv("BLP_DTS_CHUNK")) {
         const int c = atoi(e);
         h->dts_chunk = (c == 8 || c == 16 || c == 32) ? c : 0;

@@ -152,3 +152,44 @@ def test_full_size_n1024(eps):
         r = (p.f - oracle.apply(N, A, un)) / A["C"]
         assert info.status == 0 and np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(p.f / A["C"])
         assert rel(un, uo) <= tol
+
+
+# (BLP_DTS_TWO_STEP, BLP_DTS_CHUNK, BLP_DTS_CLUSTER): both forms of the
+# wavefront recurrence, every hand-off chunk, and cluster sizes that put the
+# strips in one wave (8, 16) or in several waves handed over through global
+# memory (1, 2)
+WAVEFRONT_VARIANTS = [("0", "0", "8"), ("3", "0", "8"), ("3", "8", "8"), ("3", "16", "1"), ("3", "32", "1"),
+                      ("0", "32", "2"), ("3", "16", "16")]
+
+
+@pytest.mark.parametrize("N", [512, 514, 1024])
+def test_wavefront_forms_and_shapes(N, monkeypatch):
+    """The one- and two-step forms of the downstream sweep (Sec. 3.1, 3.2),
+    under every chunk length and cluster shape, against the oracle's
+    preconditioner. N = 512: interior 255^2 (ragged last strip), corner
+    256^2 -> 128^2 -> 64^2 on the wavefront kernel; N = 514: corner 257^2 (a
+    one-column last strip, a single level of 4 sweeps per cycle); N = 1024:
+    16-strip blocks, which a one-CTA cluster (15 compute warps at most)
+    processes in two waves. Fixed cycle count, so FP32 and FP64 apply the
+    same operator. FP32 bound: one rounding (2^-24) per step along the ~2N
+    dependent steps of a sweep, with a factor 4 for the cycles and levels:
+    8 N 2^-24 (2.4e-4 at N = 512, 4.9e-4 at N = 1024)."""
+    tol32 = 8 * N * 2.0 ** -24
+    eps, fixed = 1e-4, 2
+    x, p, A = problem(N, eps)
+    P = oracle.Prec(N, eps, x, x, p.c1, p.c2, p.r, fixed_cycles=fixed)
+    v = np.random.default_rng(6).standard_normal((N - 1) ** 2)
+    zo, _ = P.apply(A["C"] * v)
+    zto, _ = P.apply(v, transpose=True)
+    zto = A["C"] * zto
+    for two_step, chunk, cluster in WAVEFRONT_VARIANTS:
+        monkeypatch.setenv("BLP_DTS_TWO_STEP", two_step)
+        monkeypatch.setenv("BLP_DTS_CHUNK", chunk)
+        monkeypatch.setenv("BLP_DTS_CLUSTER", cluster)
+        s = blp.Solver(N, eps, T(p.c1), T(p.c2), T(p.r), corner_fixed_cycles=fixed)
+        tag = (two_step, chunk, cluster)
+        assert rel(s.precond(T(v))[0], zo) < 1e-11, tag
+        assert rel(s.precond(T(v), transpose=True)[0], zto) < 1e-11, tag
+        assert rel(s.precond(T(v), precision=blp.BLP_MIXED)[0], zo) < tol32, tag
+        assert rel(s.precond(T(v), transpose=True, precision=blp.BLP_MIXED)[0], zto) < tol32, tag
+        s.close()
