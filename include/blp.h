@@ -154,6 +154,63 @@ typedef struct {
  * null array.  The caller's arrays must stay valid until the call returns. */
 int blp_solve_batched(blp_batch_item *items, int count, int concurrency);
 
+/* Launch settings of the downstream sweeps (the wavefront kernel of the
+ * Sec. 3.1 interior solve and the Sec. 3.2 Gauss-Seidel smoother).  They
+ * change the schedule of the sweeps, not what they compute: results agree
+ * to rounding order under every setting.
+ *   dts_chunk   rows of a strip's boundary column handed to the next strip at
+ *               once: 8, 16 or 32, or 0 = by precision (32 FP32, 16 FP64);
+ *               the launch falls back to a shorter chunk where the staging
+ *               buffers would not fit in shared memory;
+ *   dts_cluster CTAs per thread-block cluster, 1..16 (above 8: non-portable
+ *               cluster sizes);
+ *   two_step    bit 0: FP32 sweeps, bit 1: FP64 sweeps, use the recurrence
+ *               substituted into itself once (two rows per three dependent
+ *               FMAs) instead of one row per two;
+ *   precond_ms  blp_autotune: measured device time of one preconditioner
+ *               application with this setting; -1 when not tuned. */
+typedef struct {
+    int dts_chunk;
+    int dts_cluster;
+    int two_step;
+    double precond_ms;
+} blp_tuning;
+
+/* Current setting of the handle (the defaults, or the BLP_DTS_CHUNK,
+ * BLP_DTS_CLUSTER and BLP_DTS_TWO_STEP environment overrides read by
+ * blp_setup, or the last blp_set_tuning / blp_autotune).  BLP_ERR_ARG for a
+ * null argument. */
+int blp_get_tuning(blp_handle *h, blp_tuning *t);
+
+/* Use setting *t (precond_ms ignored) for the handle's later solves.
+ * Replayed preconditioner graphs captured under another setting are
+ * released (after the handle's stream has drained).  BLP_ERR_ARG for a
+ * null argument or a value outside the ranges above. */
+int blp_set_tuning(blp_handle *h, const blp_tuning *t);
+
+/* Autotuner: times the preconditioner application in `precision`
+ * (BLP_FP64 or BLP_MIXED) on this handle's problem, with a fixed
+ * deterministic right-hand side, under every candidate setting (chunks 8,
+ * 16, 32; cluster sizes 2 to 16 up to the widest block's strip count; one-
+ * and two-step form for that precision), `reps` timed applications each
+ * (<= 0: 3) after two warm-up ones, on the handle's stream with CUDA
+ * events.  Keeps the fastest setting on the handle and writes it to *best
+ * (may be NULL).  Allocates two vectors from the library's pool for the
+ * duration.  BLP_ERR_ARG for a null handle or another precision; on a
+ * CUDA or device error the handle's previous setting is restored and the
+ * error returned. */
+int blp_autotune(blp_handle *h, int precision, int reps, blp_tuning *best);
+
+/* blp_solve_batched with autotuned launch settings: before the problems are
+ * solved, each (N, precision) pair that this process has not tuned yet is
+ * tuned once by blp_autotune on the first problem that has it (one at a
+ * time, on a private stream); every problem then runs with the setting of
+ * its pair.  The settings stay cached for later calls in the process.
+ * Returns and reports as blp_solve_batched.  A pair whose tuning fails runs
+ * with the default setting (each problem's own setup and solve report its
+ * errors). */
+int blp_solve_batched_tuned(blp_batch_item *items, int count, int concurrency);
+
 /* Largest N accepted by blp_residual_noalloc (its fixed scratch holds four
  * partial sums per grid row: 4 * 8192 doubles = 256 KiB per device). */
 #define BLP_NOALLOC_MAX_N 8192

@@ -153,15 +153,41 @@ class Solver:
     def kernel_launches(self):
         return self.lib.blp_kernel_launches(self.handle)
 
+    def tuning(self):
+        """blp_get_tuning: the wavefront launch setting of this handle, as a
+        dict (dts_chunk, dts_cluster, two_step, precond_ms)."""
+        t = N_.Tuning()
+        N_.check(self.lib.blp_get_tuning(self.handle, ctypes.byref(t)), "blp_get_tuning")
+        return t.as_dict()
 
-def solve_batched(problems, tol=1e-10, concurrency=8):
+    def set_tuning(self, dts_chunk=None, dts_cluster=None, two_step=None):
+        """blp_set_tuning: change some of the wavefront launch settings."""
+        t = N_.Tuning()
+        N_.check(self.lib.blp_get_tuning(self.handle, ctypes.byref(t)), "blp_get_tuning")
+        for k, v in (("dts_chunk", dts_chunk), ("dts_cluster", dts_cluster), ("two_step", two_step)):
+            if v is not None:
+                setattr(t, k, int(v))
+        N_.check(self.lib.blp_set_tuning(self.handle, ctypes.byref(t)), "blp_set_tuning")
+
+    def autotune(self, precision=None, reps=3):
+        """blp_autotune: time the preconditioner under every candidate
+        wavefront setting, keep the fastest; returns it as a dict."""
+        t = N_.Tuning()
+        prec = self.params.precision if precision is None else precision
+        N_.check(self.lib.blp_autotune(self.handle, int(prec), int(reps), ctypes.byref(t)), "blp_autotune")
+        return t.as_dict()
+
+
+def solve_batched(problems, tol=1e-10, concurrency=8, autotune=False):
     """blp_solve_batched: independent problems solved concurrently.
 
     problems: list of dicts with keys N, eps, c1, c2, r, f (float64 arrays or
     tensors of (N-1)**2 values, host or device), optional u (initial guess,
-    overwritten with the solution) and any blp_params field.  Returns a list
-    of (u, Info); raises BlpError if any problem failed (the per-problem
-    statuses are in the Info objects of the exception's .results)."""
+    overwritten with the solution) and any blp_params field.  autotune=True
+    calls blp_solve_batched_tuned: wavefront launch settings tuned once per
+    (N, precision) and cached for the process.  Returns a list of (u, Info);
+    raises BlpError if any problem failed (the per-problem statuses are in
+    the Info objects of the exception's .results)."""
     lib = N_.load()
     n = len(problems)
     items = (N_.BatchItem * n)()
@@ -184,10 +210,11 @@ def solve_batched(problems, tol=1e-10, concurrency=8):
         items[k].c1, items[k].c2, items[k].r, items[k].f, items[k].u = [q[0] for q in ptrs]
         items[k].tol = tol
         outs.append(u)
-    st = lib.blp_solve_batched(items, n, int(concurrency))
+    fn = lib.blp_solve_batched_tuned if autotune else lib.blp_solve_batched
+    st = fn(items, n, int(concurrency))
     results = [(outs[k], items[k].info) for k in range(n)]
     if st != N_.BLP_OK:
-        err = BlpError(st, "blp_solve_batched")
+        err = BlpError(st, "blp_solve_batched_tuned" if autotune else "blp_solve_batched")
         err.results = results
         raise err
     return results

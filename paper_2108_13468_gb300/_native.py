@@ -41,6 +41,13 @@ class BatchItem(ctypes.Structure):
                 ("u", c_void_p), ("tol", c_double), ("info", Info), ("status", c_int)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("dts_chunk", c_int), ("dts_cluster", c_int), ("two_step", c_int), ("precond_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # exported symbol -> (restype, argtypes); the ABI test checks this against include/blp.h
 SIGNATURES = {
     "blp_params_default": (None, [ctypes.POINTER(Params)]),
@@ -61,6 +68,10 @@ SIGNATURES = {
     "blp_kernel_class_name": (ctypes.c_char_p, [c_int]),
     "blp_check_wait_timeout": (c_int, [c_void_p]),
     "blp_solve_batched": (c_int, [ctypes.POINTER(BatchItem), c_int, c_int]),
+    "blp_solve_batched_tuned": (c_int, [ctypes.POINTER(BatchItem), c_int, c_int]),
+    "blp_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
+    "blp_set_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
+    "blp_autotune": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(Tuning)]),
     "blp_residual_noalloc": (c_int, [c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     # host-side layout inspection (no GPU needed)

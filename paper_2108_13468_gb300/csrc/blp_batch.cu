@@ -7,7 +7,9 @@
 // so several problems run side by side: K host worker threads, each with
 // its own non-blocking stream, take the next unsolved problem, set it up,
 // solve it and release it.  Handles allocate from the library's
-// stream-ordered pool, so no worker synchronises the device.
+// stream-ordered pool, so no worker synchronises the device.  The tuned
+// variant first autotunes the wavefront launch settings once per new
+// (N, precision) pair (blp_tune.cu) and gives each problem its pair's.
 #include "blp_common.cuh"
 
 #include <algorithm>
@@ -18,7 +20,7 @@
 
 namespace {
 
-void run_worker(blp_batch_item *items, int count, std::atomic<int> *next, int device) {
+void run_worker(blp_batch_item *items, int count, std::atomic<int> *next, int device, bool tuned) {
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         for (int i; (i = next->fetch_add(1)) < count;) items[i].info.status = items[i].status = BLP_ERR_CUDA;
@@ -35,6 +37,9 @@ void run_worker(blp_batch_item *items, int count, std::atomic<int> *next, int de
         memset(&it.info, 0, sizeof(it.info));
         blp_handle *h = nullptr;
         int rc = blp_internal_setup(&it.params, it.c1, it.c2, it.r, s, &h);
+        blp_tuning t;
+        if (rc == BLP_OK && tuned && blp_internal_cached_tuning(&it.params, nullptr, nullptr, nullptr, s, &t) == BLP_OK)
+            blp_set_tuning(h, &t);
         if (rc == BLP_OK) {
             rc = blp_solve(h, it.f, it.u, it.tol, &it.info);
             blp_destroy(h);
@@ -48,7 +53,7 @@ void run_worker(blp_batch_item *items, int count, std::atomic<int> *next, int de
 
 }  // namespace
 
-extern "C" int blp_solve_batched(blp_batch_item *items, int count, int concurrency) {
+static int solve_batched(blp_batch_item *items, int count, int concurrency, bool tuned) {
     if (count < 0 || (count > 0 && !items)) return BLP_ERR_ARG;
     if (count == 0) return BLP_OK;
     int device = 0;
@@ -56,18 +61,40 @@ extern "C" int blp_solve_batched(blp_batch_item *items, int count, int concurren
         cudaGetLastError();
         return BLP_ERR_CUDA;
     }
+    if (tuned) {
+        // tune each new (N, precision) pair before any problem runs, one at a
+        // time, so that no other work shares the device while it is timed
+        cudaStream_t ts = nullptr;
+        if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return BLP_ERR_CUDA;
+        }
+        blp_tuning t;
+        for (int i = 0; i < count; i++)
+            blp_internal_cached_tuning(&items[i].params, items[i].c1, items[i].c2, items[i].r, ts, &t);
+        cudaStreamSynchronize(ts);
+        cudaStreamDestroy(ts);
+    }
     for (int i = 0; i < count; i++) items[i].status = -1;
     const int K = std::max(1, std::min(concurrency > 0 ? concurrency : 8, count));
     std::atomic<int> next{0};
     std::vector<std::thread> pool;
     try {
-        for (int k = 1; k < K; k++) pool.emplace_back(run_worker, items, count, &next, device);
+        for (int k = 1; k < K; k++) pool.emplace_back(run_worker, items, count, &next, device, tuned);
     } catch (...) {
         // fewer workers than asked: the ones running (and this thread) finish the batch
     }
-    run_worker(items, count, &next, device);
+    run_worker(items, count, &next, device, tuned);
     for (auto &t : pool) t.join();
     for (int i = 0; i < count; i++)
         if (items[i].status != BLP_OK) return items[i].status;
     return BLP_OK;
+}
+
+extern "C" int blp_solve_batched(blp_batch_item *items, int count, int concurrency) {
+    return solve_batched(items, count, concurrency, false);
+}
+
+extern "C" int blp_solve_batched_tuned(blp_batch_item *items, int count, int concurrency) {
+    return solve_batched(items, count, concurrency, true);
 }

@@ -237,6 +237,7 @@ struct blp_handle {
     int dts_max_cluster = 8;        // CTAs per wavefront cluster (1..16)
     bool dts_two_step32 = true;     // two-step form of the wavefront recurrence, FP32 sweeps
     bool dts_two_step64 = false;    // FP64: off (its extra DFMAs cost more than the shorter chain saves)
+    double tuned_ms = -1.0;         // blp_autotune: preconditioner time of the chosen setting (-1: not tuned)
     int dts_chunk = 0;              // wavefront chunk length (8, 16, 32 diagonals; 0: by precision)
     double t_setup_ms = 0.0;
     int last_cycles = 0;
@@ -325,3 +326,11 @@ int blp_internal_ensure_ws(blp_handle *h, size_t bytes);
 int blp_internal_to_region(blp_handle *h, const double *std_in, double *reg_out, int scale_mode);
 int blp_internal_from_region(blp_handle *h, const double *reg_in, double *std_out, int scale_mode);
 template <typename T> int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles);
+// Device error flag of the handle's kernels (bounded waits): BLP_OK or the
+// recorded status, which it clears.
+int blp_internal_check_err(blp_handle *h);
+// Wavefront setting for (N, precision) chosen by the autotuner in this
+// process; tunes on the given problem first when none is cached yet (null
+// fields: lookup only).
+int blp_internal_cached_tuning(const blp_params *p, const double *c1, const double *c2, const double *r,
+                               cudaStream_t s, blp_tuning *t);

@@ -393,6 +393,7 @@ static int check_err(blp_handle *h) {
     }
     return BLP_OK;
 }
+int blp_internal_check_err(blp_handle *h) { return check_err(h); }
 
 // Restarted FGMRES(m) on Op x = b (Op = the normalised operator or its
 // transpose) in FP64, right preconditioned by the (transposed) normalised
