@@ -66,7 +66,11 @@ typedef struct {
     int corner_max_cycles;     /* cap on corner cycles per application (default 50) */
     int corner_fixed_cycles;   /* >0: exactly this many corner cycles (M becomes a fixed linear map) */
     int check_coefficients;    /* nonzero: blp_setup validates c1, c2, r (default 1) */
+    int mesh;                  /* BLP_MESH_SHISHKIN (default) or BLP_MESH_GRADED (see blp_mesh_graded) */
 } blp_params;
+
+#define BLP_MESH_SHISHKIN 0    /* piecewise-uniform layer mesh (blp_mesh) */
+#define BLP_MESH_GRADED 1      /* graded layer mesh, same tau and split (blp_mesh_graded) */
 
 /* Statistics of the last solve. */
 typedef struct {
@@ -82,7 +86,7 @@ typedef struct {
 
 /* Fill *p with defaults: eps = 1e-4, N = 128, sigma = 2, beta = 1, restart
  * 30, maxit 20000, FP64, scaled stopping, corner_reduction 1e3, 50 max
- * cycles, no fixed cycles, coefficient checks on. */
+ * cycles, no fixed cycles, coefficient checks on, Shishkin mesh. */
 void blp_params_default(blp_params *p);
 
 /* S0. Shishkin mesh nodes (Sec. 2.2 eq. (tau 1D), Sec. 3 eq. (tau exponential)):
@@ -91,6 +95,18 @@ void blp_params_default(blp_params *p);
  * above, x_N = 1.  x: host array of N+1 doubles (caller-owned).  Returns tau,
  * or a negative value for invalid arguments. */
 double blp_mesh(int N, double eps, double sigma, double beta, double *x);
+
+/* Graded layer mesh (the Remark after Theorem (big bound): the analysis also
+ * covers graded layer meshes such as Bakhvalov's).  This is the
+ * Bakhvalov-Shishkin mesh: the same tau and N/2 + N/2 split as blp_mesh, the
+ * interior nodes of blp_mesh, and on the layer
+ *     x_i = -(sigma eps / beta) ln(1 - 2 (1 - 1/N) i / N),  0 < i < N/2,
+ * so that exp(-beta x / (sigma eps)) falls linearly in i; x_{N/2} = tau.
+ * When tau is capped at 1/2 the mesh is uniform.  Arguments, ownership and
+ * errors as blp_mesh.  The preconditioner's blocks and the corner multigrid
+ * (coarse nodes at even fine indices, transfer weights 1/2 and 1/4) are
+ * unchanged on this mesh. */
+double blp_mesh_graded(int N, double eps, double sigma, double beta, double *x);
 
 /* Assemble the operator (Sec. 3 stencil) and build the preconditioner
  * (Sec. 3.1 blocks, line factorisations, Sec. 3.2 corner hierarchy) on the

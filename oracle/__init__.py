@@ -91,10 +91,14 @@ def _f64(a) -> np.ndarray:
 COEFS = ("W", "E", "S", "N", "C")
 
 
-def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, parabolic: bool = False):
-    """Shishkin mesh nodes x[0..N] and the transition point tau (Sec. 2.2, Sec. 3)."""
+def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, parabolic: bool = False, graded: bool = False):
+    """Shishkin mesh nodes x[0..N] and the transition point tau (Sec. 2.2, Sec. 3).
+
+    graded=True: the graded (Bakhvalov-Shishkin) layer mesh with the same tau
+    and N/2 split (the Remark after Theorem (big bound) covers graded meshes)."""
+    assert not (parabolic and graded)
     x = np.zeros(N + 1)
-    tau = _load().orc_mesh(N, eps, sigma, beta, int(parabolic), _p(x))
+    tau = _load().orc_mesh(N, eps, sigma, beta, 1 if parabolic else (2 if graded else 0), _p(x))
     return x, tau
 
 

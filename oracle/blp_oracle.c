@@ -37,18 +37,35 @@ static size_t ix(int N, int i, int j) { return (size_t)(j - 1) * (size_t)(N - 1)
  * [0,tau] and N/2 on [tau,1].  Node rule: x_i = (i/(N/2))*tau for i <= N/2,
  * x_i = tau + ((i-N/2)/(N/2))*(1-tau) above, x_N = 1 exactly.
  * Sec. 3, eq. (tau parabolic) replaces sigma*eps/beta by sigma*sqrt(eps) for a
- * parabolic layer (selected with parabolic != 0, beta ignored).
+ * parabolic layer (kind 1, beta ignored).
+ *
+ * kind 2: graded layer mesh.  The Remark after Theorem (big bound) notes that
+ * the theory holds for graded layer meshes as well as for piecewise-uniform
+ * ones; the graded mesh taken here is the Bakhvalov-Shishkin mesh (Linss,
+ * J. Comput. Appl. Math. 110, 1999).  It keeps the Shishkin transition point
+ * tau and the N/2 + N/2 split, and places the layer nodes so that the layer
+ * function exp(-beta x / (sigma eps)) falls linearly in i:
+ *     x_i = -(sigma eps / beta) ln(1 - 2 (1 - 1/N) i / N),  0 <= i <= N/2,
+ * which reaches tau = sigma eps ln(N) / beta at i = N/2; uniform on [tau,1].
+ * When tau is capped at 1/2 the mesh is uniform, as the Shishkin mesh is.
  * Returns tau.
  * ---------------------------------------------------------------------- */
-double orc_mesh(int N, double eps, double sigma, double beta, int parabolic, double *x)
+double orc_mesh(int N, double eps, double sigma, double beta, int kind, double *x)
 {
     double lnN = log((double)N);
-    double tau = parabolic ? sigma * sqrt(eps) * lnN : sigma * eps * lnN / beta;
-    if (tau > 0.5) tau = 0.5;
+    double tau = kind == 1 ? sigma * sqrt(eps) * lnN : sigma * eps * lnN / beta;
+    int capped = tau >= 0.5;
+    if (capped) tau = 0.5;
     int m = N / 2;
-    for (int i = 0; i <= m; i++) x[i] = ((double)i / (double)m) * tau;
+    for (int i = 0; i <= m; i++) {
+        if (kind == 2 && !capped)
+            x[i] = -(sigma * eps / beta) * log(1.0 - 2.0 * (1.0 - 1.0 / (double)N) * (double)i / (double)N);
+        else
+            x[i] = ((double)i / (double)m) * tau;
+    }
     for (int i = m + 1; i <= N; i++) x[i] = tau + ((double)(i - m) / (double)m) * (1.0 - tau);
     x[0] = 0.0;
+    x[m] = tau;
     x[N] = 1.0;
     return tau;
 }

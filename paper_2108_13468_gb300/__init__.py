@@ -21,11 +21,12 @@ import ctypes
 import numpy as np
 
 from . import _native as N_
-from ._native import (BLP_FP64, BLP_MIXED, BLP_STOP_ABS2, BLP_STOP_REL2, BLP_STOP_SCALED, BlpError, Info,
-                      Params)
+from ._native import (BLP_FP64, BLP_MESH_GRADED, BLP_MESH_SHISHKIN, BLP_MIXED, BLP_STOP_ABS2, BLP_STOP_REL2,
+                      BLP_STOP_SCALED, BlpError, Info, Params)
 
 __all__ = ["mesh", "Solver", "Params", "Info", "BlpError", "BLP_FP64", "BLP_MIXED", "BLP_STOP_SCALED",
-           "BLP_STOP_REL2", "BLP_STOP_ABS2", "default_params", "solve", "solve_batched", "residual_noalloc"]
+           "BLP_STOP_REL2", "BLP_STOP_ABS2", "BLP_MESH_SHISHKIN", "BLP_MESH_GRADED", "default_params", "solve",
+           "solve_batched", "residual_noalloc"]
 
 
 def default_params(**kw) -> Params:
@@ -38,12 +39,14 @@ def default_params(**kw) -> Params:
     return p
 
 
-def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0):
-    """Shishkin mesh nodes x[0..N] (blp_mesh) and the transition point tau."""
+def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, graded: bool = False):
+    """Shishkin mesh nodes x[0..N] (blp_mesh) and the transition point tau;
+    graded=True: the graded layer mesh with the same tau (blp_mesh_graded)."""
     x = np.zeros(N + 1)
-    tau = N_.load().blp_mesh(N, eps, sigma, beta, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    fn = N_.load().blp_mesh_graded if graded else N_.load().blp_mesh
+    tau = fn(N, eps, sigma, beta, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if tau < 0:
-        raise BlpError(N_.BLP_ERR_ARG, "blp_mesh")
+        raise BlpError(N_.BLP_ERR_ARG, "blp_mesh_graded" if graded else "blp_mesh")
     return x, tau
 
 

@@ -15,6 +15,7 @@ BLP_OK, BLP_ERR_ARG, BLP_ERR_COEF, BLP_ERR_NOCONV, BLP_ERR_TIMEOUT, BLP_ERR_CUDA
 BLP_FP64, BLP_MIXED = 0, 1
 BLP_STOP_SCALED, BLP_STOP_REL2, BLP_STOP_ABS2 = 0, 1, 2
 BLP_NOALLOC_MAX_N = 8192
+BLP_MESH_SHISHKIN, BLP_MESH_GRADED = 0, 1
 
 c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -24,7 +25,7 @@ class Params(ctypes.Structure):
     _fields_ = [("eps", c_double), ("N", c_int), ("sigma", c_double), ("beta_x", c_double), ("beta_y", c_double),
                 ("restart", c_int), ("maxit", c_int), ("precision", c_int), ("stop_mode", c_int),
                 ("corner_reduction", c_double), ("corner_max_cycles", c_int), ("corner_fixed_cycles", c_int),
-                ("check_coefficients", c_int)]
+                ("check_coefficients", c_int), ("mesh", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -52,6 +53,7 @@ class Tuning(ctypes.Structure):
 SIGNATURES = {
     "blp_params_default": (None, [ctypes.POINTER(Params)]),
     "blp_mesh": (c_double, [c_int, c_double, c_double, c_double, _DP]),
+    "blp_mesh_graded": (c_double, [c_int, c_double, c_double, c_double, _DP]),
     "blp_setup": (c_int, [ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]),
     "blp_set_stream": (c_int, [c_void_p, c_void_p]),
     "blp_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(Info)]),

@@ -23,6 +23,18 @@ extern "C" double blp_mesh(int N, double eps, double sigma, double beta, double 
     return tau;
 }
 
+// Graded (Bakhvalov-Shishkin) layer mesh: the Shishkin tau, split and
+// interior nodes; on [0, tau] the nodes sample the layer function
+// exp(-beta x / (sigma eps)) at equal decrements 2 (1 - 1/N) / N.
+extern "C" double blp_mesh_graded(int N, double eps, double sigma, double beta, double *x) {
+    const double tau = blp_mesh(N, eps, sigma, beta, x);
+    if (tau < 0.0 || tau >= 0.5) return tau;   // invalid, or the uniform mesh
+    const int m = N / 2;
+    const double scale = sigma * eps / beta, step = 2.0 * (1.0 - 1.0 / (double)N);
+    for (int i = 1; i < m; i++) x[i] = -scale * std::log(1.0 - step * (double)i / (double)N);
+    return tau;
+}
+
 extern "C" void blp_params_default(blp_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
@@ -30,6 +42,7 @@ extern "C" void blp_params_default(blp_params *p) {
     p->restart = 30; p->maxit = 20000; p->precision = BLP_FP64; p->stop_mode = BLP_STOP_SCALED;
     p->corner_reduction = 1e3; p->corner_max_cycles = 50; p->corner_fixed_cycles = 0;
     p->check_coefficients = 1;
+    p->mesh = BLP_MESH_SHISHKIN;
 }
 
 extern "C" const char *blp_strerror(int s) {
@@ -574,8 +587,9 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
     long long np = h->lay.npad;
     h->hx.resize(N + 1);
     h->hy.resize(N + 1);
-    h->tau_x = blp_mesh(N, p.eps, p.sigma, p.beta_x, h->hx.data());
-    h->tau_y = blp_mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
+    auto mesh = p.mesh == BLP_MESH_GRADED ? blp_mesh_graded : blp_mesh;
+    h->tau_x = mesh(N, p.eps, p.sigma, p.beta_x, h->hx.data());
+    h->tau_y = mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
     TRY(dalloc(h, &h->x, N + 1));
     TRY(dalloc(h, &h->y, N + 1));
     CUDA_TRY(cudaMemcpyAsync(h->x, h->hx.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice, h->stream));
@@ -647,7 +661,8 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
     if (p->N < 8 || p->N > 16384 || (p->N & 1) || !(p->eps > 0.0) || p->eps > 1.0 || !(p->sigma > 0.0) ||
         !(p->beta_x > 0.0) || !(p->beta_y > 0.0) || p->restart < 1 || p->restart > 64 || p->maxit < 1 ||
         (p->precision != BLP_FP64 && p->precision != BLP_MIXED) || p->stop_mode < 0 || p->stop_mode > 2 ||
-        !(p->corner_reduction >= 1.0) || p->corner_max_cycles < 1)
+        !(p->corner_reduction >= 1.0) || p->corner_max_cycles < 1 ||
+        (p->mesh != BLP_MESH_SHISHKIN && p->mesh != BLP_MESH_GRADED))
         return BLP_ERR_ARG;
     auto t0 = std::chrono::steady_clock::now();
     blp_handle *h = new blp_handle();

@@ -49,6 +49,9 @@ def test_library_mesh_matches_oracle_mesh():
         x = np.zeros(N + 1)
         _native.load().blp_mesh(N, eps, 2.0, 1.0, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         np.testing.assert_array_equal(x, oracle.mesh(N, eps)[0])
+        g = np.zeros(N + 1)
+        _native.load().blp_mesh_graded(N, eps, 2.0, 1.0, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        np.testing.assert_array_equal(g, oracle.mesh(N, eps, graded=True)[0])
 
 
 @pytest.mark.parametrize("N", [8, 10, 34, 64, 66, 96, 130])
