@@ -227,6 +227,48 @@ int blp_autotune(blp_handle *h, int precision, int reps, blp_tuning *best);
  * errors). */
 int blp_solve_batched_tuned(blp_batch_item *items, int count, int concurrency);
 
+/* One-dimensional method of Sec. 2, batched.  Problem k is
+ *     -eps u'' - c(x) u' + r(x) u = f on (0,1),  u(0) = u(1) = 0     (eq. 1D),
+ * discretised by the upwind scheme of eq. (stencil_1d) on the Shishkin mesh
+ * of eq. (tau 1D) with tau = min(1/2, sigma eps ln(N) / c_low) and N/2
+ * intervals on each side of tau, and solved by GMRES without restarts from
+ * u = 0, right-preconditioned with M of eq. (block_M) (A on the layer block
+ * and both coupling entries, the upper triangle of the interior block),
+ * stopping at the first iterate with ||f - A u||_inf <= stop (the rule of
+ * Sec. 2.5.1 with K g(N) = stop), or after maxit iterations.
+ *   N        intervals, even, 8 <= N <= BLP_1D_MAX_N
+ *   c, r, f  DEVICE (or managed) arrays of N-1 values at the interior nodes
+ *            x_1 .. x_{N-1} of that mesh (caller-owned, read only)
+ *   u        DEVICE array of N-1 values: receives the last iterate
+ *   maxit    1 .. BLP_1D_MAXIT
+ *   iters, resid, status (out): iterations taken, ||f - A u||_inf of the
+ *            returned u, BLP_OK or BLP_ERR_NOCONV (maxit reached) or
+ *            BLP_ERR_ARG (this problem's arguments are invalid). */
+#define BLP_1D_MAX_N 65536
+#define BLP_1D_MAXIT 128
+typedef struct {
+    int N;
+    double eps, c_low, sigma;
+    const double *c, *r, *f;
+    double *u;
+    double stop;
+    int maxit;
+    int iters;
+    double resid;
+    int status;
+} blp_1d_problem;
+
+/* Solve `count` problems on `stream` (a cudaStream_t; NULL: the legacy
+ * stream), one GPU thread per problem; returns after they have finished.
+ * Workspace: (maxit + 10) (N - 1) + (maxit + 1) maxit doubles per problem,
+ * allocated stream-ordered for the call.  Returns BLP_OK when every problem
+ * met its stopping rule, else the status of the first problem that did not
+ * (the others still run); BLP_ERR_ARG, with nothing launched, when count < 0,
+ * probs is null or any problem's arguments are invalid (host pointers
+ * included: they are refused, never dereferenced on the device); BLP_ERR_MEM
+ * when the workspace cannot be allocated. */
+int blp_solve_1d_batched(blp_1d_problem *probs, int count, void *stream);
+
 /* Largest N accepted by blp_residual_noalloc (its fixed scratch holds four
  * partial sums per grid row: 4 * 8192 doubles = 256 KiB per device). */
 #define BLP_NOALLOC_MAX_N 8192

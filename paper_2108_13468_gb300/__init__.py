@@ -26,7 +26,7 @@ from ._native import (BLP_FP64, BLP_MESH_GRADED, BLP_MESH_SHISHKIN, BLP_MIXED, B
 
 __all__ = ["mesh", "Solver", "Params", "Info", "BlpError", "BLP_FP64", "BLP_MIXED", "BLP_STOP_SCALED",
            "BLP_STOP_REL2", "BLP_STOP_ABS2", "BLP_MESH_SHISHKIN", "BLP_MESH_GRADED", "default_params", "solve",
-           "solve_batched", "residual_noalloc"]
+           "solve_batched", "solve_1d_batched", "residual_noalloc"]
 
 
 def default_params(**kw) -> Params:
@@ -221,6 +221,46 @@ def solve_batched(problems, tol=1e-10, concurrency=8, autotune=False):
         err.results = results
         raise err
     return results
+
+
+def solve_1d_batched(problems, stream=None):
+    """blp_solve_1d_batched: the 1D method of Sec. 2 (upwind scheme, Shishkin
+    mesh, GMRES right-preconditioned with M of eq. (block_M), true-residual
+    stop) for many problems at once, one GPU thread per problem.
+
+    problems: dicts with N, eps, stop (absolute ||f - A u||_inf target) and
+    c, r, f (device float64 tensors of N-1 values at the interior nodes of
+    mesh(N, eps, sigma, c_low), i.e. the 1D Shishkin mesh with beta = c_low),
+    optional c_low (default 1), sigma (default 2), maxit (default 64).
+    Returns a list of (u, iters, resid, status); raises BlpError when a
+    problem is invalid (nothing runs) and returns normally otherwise (check
+    each status: BLP_ERR_NOCONV when maxit was reached)."""
+    import torch
+    lib = N_.load()
+    n = len(problems)
+    items = (N_.Problem1D * n)()
+    outs, keep = [], []
+    for k, pr in enumerate(problems):
+        N = int(pr["N"])
+        fields = [pr[key] for key in ("c", "r", "f")]
+        # the output lives where f does; the library refuses anything but device arrays
+        u = torch.zeros_like(fields[2]) if isinstance(fields[2], torch.Tensor) else np.zeros(N - 1)
+        it = items[k]
+        it.N, it.eps, it.stop = N, float(pr["eps"]), float(pr["stop"])
+        it.c_low, it.sigma, it.maxit = float(pr.get("c_low", 1.0)), float(pr.get("sigma", 2.0)), int(pr.get("maxit", 64))
+        ptrs = [_ptr(a, N - 1) for a in fields] + [_ptr(u, N - 1, True)]
+        keep.append(ptrs)
+        it.c, it.r, it.f, it.u = [q[0] for q in ptrs]
+        outs.append(u)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.blp_solve_1d_batched(items, n, ctypes.c_void_p(stream))
+    if st == N_.BLP_ERR_ARG:
+        raise BlpError(st, "blp_solve_1d_batched (invalid problem: N even in [8, BLP_1D_MAX_N], 0 < eps <= 1, "
+                           "c_low, sigma > 0, 1 <= maxit <= BLP_1D_MAXIT, device arrays)")
+    if st not in (N_.BLP_OK, N_.BLP_ERR_NOCONV):
+        N_.check(st, "blp_solve_1d_batched")
+    return [(outs[k], items[k].iters, items[k].resid, items[k].status) for k in range(n)]
 
 
 def residual_noalloc(N, x, y, eps, c1, c2, r, f, u, res=None, stream=None):

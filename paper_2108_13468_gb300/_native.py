@@ -16,6 +16,7 @@ BLP_FP64, BLP_MIXED = 0, 1
 BLP_STOP_SCALED, BLP_STOP_REL2, BLP_STOP_ABS2 = 0, 1, 2
 BLP_NOALLOC_MAX_N = 8192
 BLP_MESH_SHISHKIN, BLP_MESH_GRADED = 0, 1
+BLP_1D_MAX_N, BLP_1D_MAXIT = 65536, 128
 
 c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -40,6 +41,12 @@ class Info(ctypes.Structure):
 class BatchItem(ctypes.Structure):
     _fields_ = [("params", Params), ("c1", c_void_p), ("c2", c_void_p), ("r", c_void_p), ("f", c_void_p),
                 ("u", c_void_p), ("tol", c_double), ("info", Info), ("status", c_int)]
+
+
+class Problem1D(ctypes.Structure):
+    _fields_ = [("N", c_int), ("eps", c_double), ("c_low", c_double), ("sigma", c_double), ("c", c_void_p),
+                ("r", c_void_p), ("f", c_void_p), ("u", c_void_p), ("stop", c_double), ("maxit", c_int),
+                ("iters", c_int), ("resid", c_double), ("status", c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -71,6 +78,7 @@ SIGNATURES = {
     "blp_check_wait_timeout": (c_int, [c_void_p]),
     "blp_solve_batched": (c_int, [ctypes.POINTER(BatchItem), c_int, c_int]),
     "blp_solve_batched_tuned": (c_int, [ctypes.POINTER(BatchItem), c_int, c_int]),
+    "blp_solve_1d_batched": (c_int, [ctypes.POINTER(Problem1D), c_int, c_void_p]),
     "blp_get_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
     "blp_set_tuning": (c_int, [c_void_p, ctypes.POINTER(Tuning)]),
     "blp_autotune": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(Tuning)]),
