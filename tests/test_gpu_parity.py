@@ -131,7 +131,7 @@ def test_edge_cases_and_errors():
 @pytest.mark.parametrize("eps", [1e-4, 1e-8])
 def test_full_size_n1024(eps):
     """N = 1024 (the benchmark workload): operator and FP64 preconditioner
-    against the oracle on the whole vector, and both solves judged by the
+    against the oracle on the whole vector, and both solves checked by the
     oracle's own residual (a property that holds at any size) plus the
     oracle's FGMRES answer at a tighter tolerance."""
     N = 1024
