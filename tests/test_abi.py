@@ -77,3 +77,30 @@ def test_region_layout_is_a_bijection(N):
             assert p not in seen
     assert valid == (N - 1) ** 2
     assert npad % 32 == 0
+
+
+def test_host_side_argument_checks_of_the_newer_entry_points():
+    """Refusals that happen on the host, before any device work (no GPU here):
+    null handles and arguments, invalid tuning values, invalid meshes, 1D
+    problems with bad sizes or non-device arrays, and empty batches."""
+    lib = _native.load()
+    t = _native.Tuning(16, 8, 1, -1.0)
+    assert lib.blp_get_tuning(None, ctypes.byref(t)) == _native.BLP_ERR_ARG
+    assert lib.blp_set_tuning(None, ctypes.byref(t)) == _native.BLP_ERR_ARG
+    assert lib.blp_autotune(None, _native.BLP_MIXED, 3, None) == _native.BLP_ERR_ARG
+    x = (ctypes.c_double * 65)()
+    assert lib.blp_mesh_graded(63, 1e-4, 2.0, 1.0, x) < 0 and lib.blp_mesh_graded(64, 0.0, 2.0, 1.0, x) < 0
+    assert lib.blp_solve_batched_tuned(None, 0, 4) == _native.BLP_OK
+    assert lib.blp_solve_batched_tuned(None, 3, 4) == _native.BLP_ERR_ARG
+    assert lib.blp_solve_1d_batched(None, 0, None) == _native.BLP_OK
+    assert lib.blp_solve_1d_batched(None, 1, None) == _native.BLP_ERR_ARG
+    host = (ctypes.c_double * 63)()
+    ptr = ctypes.cast(host, ctypes.c_void_p)
+    probs = (_native.Problem1D * 3)()
+    for k, (N, maxit) in enumerate([(64, 8), (63, 8), (64, _native.BLP_1D_MAXIT + 1)]):
+        probs[k].N, probs[k].eps, probs[k].c_low, probs[k].sigma = N, 1e-4, 1.0, 2.0
+        probs[k].c = probs[k].r = probs[k].f = probs[k].u = ptr     # host memory: refused
+        probs[k].stop, probs[k].maxit = 1e-3, maxit
+    assert lib.blp_solve_1d_batched(probs, 3, None) == _native.BLP_ERR_ARG
+    assert [probs[k].status for k in range(3)] == [_native.BLP_ERR_ARG] * 3
+    assert all(probs[k].iters == 0 and probs[k].resid == -1.0 for k in range(3))
