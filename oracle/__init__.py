@@ -49,7 +49,15 @@ def _load():
     lib.orc_band_solve.restype = c_int
     lib.orc_band_solve.argtypes = [c_int, _D, _D, _D, _D, _D, _D, _D, c_int]
     lib.orc_prec_create.restype = c_void
-    lib.orc_prec_create.argtypes = [c_int, c_double, _D, _D, _D, _D, _D, c_double, c_int, c_int, c_int, c_int]
+    lib.orc_prec_create.argtypes = [c_int, c_double, _D, _D, _D, _D, _D, c_double, c_int, c_int, c_int, c_int, c_int]
+    lib.orc_semi_nlev.restype = c_int
+    lib.orc_semi_nlev.argtypes = [c_void]
+    lib.orc_semi_width.restype = c_int
+    lib.orc_semi_width.argtypes = [c_void, c_int]
+    lib.orc_semi_level.restype = None
+    lib.orc_semi_level.argtypes = [c_void, c_int, _D, _D, _D]
+    lib.orc_semi_gs.restype = None
+    lib.orc_semi_gs.argtypes = [c_void, c_int, _D, _D]
     lib.orc_prec_destroy.restype = None
     lib.orc_prec_destroy.argtypes = [c_void]
     lib.orc_prec_apply.restype = c_int
@@ -139,15 +147,20 @@ def grad(N, x, y, u, lam):
 class Prec:
     """The block preconditioner M of Sec. 3.1 (eq. 2D blocks) with the corner
     multigrid of Sec. 3.2.  fixed_cycles > 0 makes M_CC^{-1} a fixed number of
-    cycles; corner_exact=True replaces M_CC by A_CC (the idealised M-hat)."""
+    cycles; corner_exact=True replaces M_CC by A_CC (the idealised M-hat).
+    parabolic=True takes the corner cycle the paper gives for one parabolic
+    and one exponential layer (x-semicoarsening, operator-induced
+    interpolation, Galerkin coarse operators; forward application only); the
+    paper stops it at a 10^2 reduction (pass reduction=1e2)."""
 
     def __init__(self, N, eps, x, y, c1, c2, r, reduction=1e3, max_cycles=50, fixed_cycles=0,
-                 coarsest_min=2, corner_exact=False):
+                 coarsest_min=2, corner_exact=False, parabolic=False):
         self._lib = _load()
         self.N = N
+        self.parabolic = parabolic
         self._keep = [_f64(a) for a in (x, y, c1, c2, r)]
         h = self._lib.orc_prec_create(N, eps, *[_p(a) for a in self._keep], reduction, max_cycles,
-                                      fixed_cycles, coarsest_min, int(corner_exact))
+                                      fixed_cycles, coarsest_min, int(corner_exact), int(parabolic))
         if not h:
             raise ValueError("orc_prec_create rejected the arguments")
         self.h = ctypes.c_void_p(h)
@@ -159,6 +172,8 @@ class Prec:
             self.h = None
 
     def apply(self, v, transpose=False):
+        if transpose and self.parabolic:
+            raise ValueError("the parabolic corner cycle is provided forward only")
         z = np.zeros((self.N - 1) ** 2)
         cyc = self._lib.orc_prec_apply(self.h, _p(_f64(v)), _p(z), int(transpose))
         return z, cyc
@@ -176,6 +191,24 @@ class Prec:
         arrs = [np.zeros(m * m) for _ in range(6)]
         self._lib.orc_prec_level(self.h, l, _p(xs), _p(ys), *[_p(a) for a in arrs])
         return xs, ys, dict(zip(COEFS + ("D",), arrs))
+
+    @property
+    def semi_nlev(self):
+        return self._lib.orc_semi_nlev(self.h)
+
+    def semi_level(self, l):
+        """Level l of the parabolic cycle: (A9, PW, PE) with A9[(dy+1)*3+(dx+1)]
+        the (m, width) array of entries to node (I+dx, J+dy), and the
+        interpolation weights of the odd columns from level l+1."""
+        w, m = self._lib.orc_semi_width(self.h, l), self.N // 2
+        A9, PW, PE = np.zeros(9 * w * m), np.zeros(w * m), np.zeros(w * m)
+        self._lib.orc_semi_level(self.h, l, _p(A9), _p(PW), _p(PE))
+        return A9.reshape(9, m, w), PW.reshape(m, w), PE.reshape(m, w)
+
+    def semi_gs(self, l, b, e):
+        e = _f64(e).copy()
+        self._lib.orc_semi_gs(self.h, l, _p(_f64(b)), _p(e))
+        return e
 
     def gs(self, l, b, e, transpose=False):
         e = _f64(e).copy()

@@ -297,6 +297,14 @@ typedef struct {
     int corner_exact;     /* 1: M_CC = A_CC solved by banded LU (the idealised M-hat) */
     int last_cycles;
     double *wv;           /* work vectors */
+    /* parabolic-layer corner cycle (semi != 0): x-semicoarsened levels of
+     * width sx[l] and height m, 9-point operators A9[l] (9 planes, plane
+     * (dy+1)*3 + (dx+1) holds the entry to node (I+dx, J+dy)), and the
+     * interpolation weights from level l+1 to the odd columns of level l */
+    int semi, snlev;
+    int sx[ORC_MAXLEV];
+    double *A9[ORC_MAXLEV], *PW[ORC_MAXLEV], *PE[ORC_MAXLEV];
+    double *sr[ORC_MAXLEV], *sb[ORC_MAXLEV], *se[ORC_MAXLEV];
 } orc_prec;
 
 static double *dalloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(double)); }
@@ -311,14 +319,19 @@ void orc_prec_destroy(orc_prec *P)
         free(P->LW[l]); free(P->LE[l]); free(P->LS[l]); free(P->LN[l]); free(P->LC[l]);
         free(P->LD[l]); free(P->tmp_r[l]); free(P->tmp_b[l]); free(P->tmp_e[l]);
     }
+    for (int l = 0; l < P->snlev; l++) {
+        free(P->A9[l]); free(P->PW[l]); free(P->PE[l]); free(P->sr[l]); free(P->sb[l]); free(P->se[l]);
+    }
     free(P->wv);
     free(P);
 }
 
+static void semi_build(orc_prec *P);
+
 orc_prec *orc_prec_create(int N, double eps, const double *x, const double *y,
                           const double *c1, const double *c2, const double *r,
                           double reduction, int max_cycles, int fixed_cycles, int coarsest_min,
-                          int corner_exact)
+                          int corner_exact, int semi)
 {
     if (N < 4 || (N & 1)) return NULL;
     orc_prec *P = (orc_prec *)calloc(1, sizeof(orc_prec));
@@ -368,6 +381,8 @@ orc_prec *orc_prec_create(int N, double eps, const double *x, const double *y,
         ml /= 2;
     }
     P->nlev = l;
+    P->semi = semi;
+    if (semi) semi_build(P);
     return P;
 }
 
@@ -520,6 +535,239 @@ static double nrm2(size_t n, const double *v)
     return sqrt(s);
 }
 
+/* ------------------------------------------------------------------------
+ * Corner multigrid for one parabolic and one exponential layer (Sec. 3.2,
+ * the case of eq. (tau parabolic)), taken step by step as the paper states
+ * it:
+ *  - inside the cycle the corner rows are rescaled to finite-element size,
+ *    row (x_i, y_j) of A_CC multiplied by hb_i kb_j, and the residual with
+ *    it: the cycle works on A_0 = D A_CC, D b;
+ *  - coarse levels coarsen by 2 in x only: coarse column I is fine column
+ *    2I, every row is kept; coarsening continues while the width is even,
+ *    at least 4, and half of it is at least coarsest_min;
+ *  - interpolation is induced by the operator: row (i,j) of the level
+ *    matrix is collapsed North-South, and an odd fine column i takes from
+ *    coarse columns (i-1)/2 and (i+1)/2 (same row) the weights
+ *        -(a[(i,j),(i-1,j-1)] + a[(i,j),(i-1,j)] + a[(i,j),(i-1,j+1)]) / s,
+ *        -(a[(i,j),(i+1,j-1)] + a[(i,j),(i+1,j)] + a[(i,j),(i+1,j+1)]) / s,
+ *        s = a[(i,j),(i,j-1)] + a[(i,j),(i,j)] + a[(i,j),(i,j+1)];
+ *    even columns are injected.  Only entries of the matrix enter the sums:
+ *    couplings to nodes outside the block (the boundary, the X and Y
+ *    regions) are not entries of A_CC and count as 0;
+ *  - restriction is P^T and each coarse operator the Galerkin product
+ *    A_{l+1} = P^T A_l P (nine-point on every coarse level);
+ *  - relaxation is pointwise Gauss-Seidel in the downstream order (rows top
+ *    to bottom, right to left within a row), V(1,1), four sweeps on the
+ *    coarsest level;
+ *  - cycles run until ||D b - A_0 e||_2 <= ||D b||_2 / reduction (the paper
+ *    uses 10^2 for this case), at most max_cycles, or fixed_cycles exactly.
+ * Only the forward cycle is provided.
+ * ---------------------------------------------------------------------- */
+static size_t plane(int dx, int dy) { return (size_t)((dy + 1) * 3 + (dx + 1)); }
+
+/* entry of the level-l matrix in row (I,J), column (I+dx, J+dy); 0 when that
+ * node is outside the level's block */
+static double semi_a(const orc_prec *P, int l, int I, int J, int dx, int dy)
+{
+    int sx = P->sx[l], m = P->m;
+    if (I + dx < 1 || I + dx > sx || J + dy < 1 || J + dy > m) return 0.0;
+    return P->A9[l][plane(dx, dy) * ((size_t)sx * m) + (size_t)(J - 1) * sx + (I - 1)];
+}
+
+/* the coarse columns (level l+1, same row) that fine node (I,J) of level l
+ * interpolates from, with their weights; returns how many */
+static int semi_pcols(const orc_prec *P, int l, int I, int J, int *Ic, double *w)
+{
+    if (!(I & 1)) { Ic[0] = I / 2; w[0] = 1.0; return 1; }
+    size_t k = (size_t)(J - 1) * P->sx[l] + (I - 1);
+    int c = 0;
+    if ((I - 1) / 2 >= 1) { Ic[c] = (I - 1) / 2; w[c] = P->PW[l][k]; c++; }
+    if ((I + 1) / 2 <= P->sx[l + 1]) { Ic[c] = (I + 1) / 2; w[c] = P->PE[l][k]; c++; }
+    return c;
+}
+
+static void semi_weights(orc_prec *P, int l)
+{
+    int sx = P->sx[l], m = P->m;
+    size_t n = (size_t)sx * m;
+    P->PW[l] = dalloc(n); P->PE[l] = dalloc(n);
+    for (int J = 1; J <= m; J++)
+        for (int I = 1; I <= sx; I += 2) {
+            double s = semi_a(P, l, I, J, 0, -1) + semi_a(P, l, I, J, 0, 0) + semi_a(P, l, I, J, 0, 1);
+            double w = semi_a(P, l, I, J, -1, -1) + semi_a(P, l, I, J, -1, 0) + semi_a(P, l, I, J, -1, 1);
+            double e = semi_a(P, l, I, J, 1, -1) + semi_a(P, l, I, J, 1, 0) + semi_a(P, l, I, J, 1, 1);
+            size_t k = (size_t)(J - 1) * sx + (I - 1);
+            P->PW[l][k] = -w / s;
+            P->PE[l][k] = -e / s;
+        }
+}
+
+/* A_{l+1} = P^T A_l P: sum over fine rows p and their nonzero entries
+ * a = A_l[p,q] of P[p,c1] a P[q,c2] into A_{l+1}[c1,c2] */
+static void semi_galerkin(orc_prec *P, int l)
+{
+    int sx = P->sx[l], sxc = P->sx[l + 1], m = P->m;
+    size_t nc = (size_t)sxc * m;
+    double *Ac = P->A9[l + 1];
+    for (int J = 1; J <= m; J++)
+        for (int I = 1; I <= sx; I++) {
+            int Ip[2], Iq[2];
+            double wp[2], wq[2];
+            int np_ = semi_pcols(P, l, I, J, Ip, wp);
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    double a = semi_a(P, l, I, J, dx, dy);
+                    if (a == 0.0) continue;
+                    int nq = semi_pcols(P, l, I + dx, J + dy, Iq, wq);
+                    for (int s = 0; s < np_; s++)
+                        for (int t = 0; t < nq; t++) {
+                            int ddx = Iq[t] - Ip[s];
+                            if (ddx < -1 || ddx > 1) continue;   /* cannot happen: P spans one coarse column each side */
+                            Ac[plane(ddx, dy) * nc + (size_t)(J - 1) * sxc + (Ip[s] - 1)] += wp[s] * a * wq[t];
+                        }
+                }
+        }
+}
+
+static void semi_build(orc_prec *P)
+{
+    int m = P->m, sx = m;
+    size_t n = (size_t)m * m;
+    P->sx[0] = m;
+    P->A9[0] = dalloc(9 * n);
+    for (int J = 1; J <= m; J++)
+        for (int I = 1; I <= m; I++) {
+            size_t k = (size_t)(J - 1) * m + (I - 1);
+            double d = P->LD[0][k];
+            P->A9[0][plane(0, 0) * n + k] = d * P->LC[0][k];
+            if (I > 1) P->A9[0][plane(-1, 0) * n + k] = d * P->LW[0][k];
+            if (I < m) P->A9[0][plane(1, 0) * n + k] = d * P->LE[0][k];
+            if (J > 1) P->A9[0][plane(0, -1) * n + k] = d * P->LS[0][k];
+            if (J < m) P->A9[0][plane(0, 1) * n + k] = d * P->LN[0][k];
+        }
+    int l = 0;
+    for (;;) {
+        size_t nl = (size_t)P->sx[l] * m;
+        P->sr[l] = dalloc(nl); P->sb[l] = dalloc(nl); P->se[l] = dalloc(nl);
+        if ((sx & 1) || sx / 2 < P->coarsest_min || sx < 4 || l + 1 >= ORC_MAXLEV) break;
+        semi_weights(P, l);
+        sx /= 2;
+        P->sx[l + 1] = sx;
+        P->A9[l + 1] = dalloc(9 * (size_t)sx * m);
+        semi_galerkin(P, l);
+        l++;
+    }
+    P->snlev = l + 1;
+}
+
+static void semi_apply(const orc_prec *P, int l, const double *e, double *out)
+{
+    int sx = P->sx[l], m = P->m;
+    for (int J = 1; J <= m; J++)
+        for (int I = 1; I <= sx; I++) {
+            double s = 0.0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    double a = semi_a(P, l, I, J, dx, dy);
+                    if (a != 0.0) s += a * e[(size_t)(J + dy - 1) * sx + (I + dx - 1)];
+                }
+            out[(size_t)(J - 1) * sx + (I - 1)] = s;
+        }
+}
+
+void orc_semi_gs(orc_prec *P, int l, const double *b, double *e)
+{
+    int sx = P->sx[l], m = P->m;
+    for (int J = m; J >= 1; J--)
+        for (int I = sx; I >= 1; I--) {
+            double s = b[(size_t)(J - 1) * sx + (I - 1)];
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (!dx && !dy) continue;
+                    double a = semi_a(P, l, I, J, dx, dy);
+                    if (a != 0.0) s -= a * e[(size_t)(J + dy - 1) * sx + (I + dx - 1)];
+                }
+            e[(size_t)(J - 1) * sx + (I - 1)] = s / semi_a(P, l, I, J, 0, 0);
+        }
+}
+
+/* ef += P ec (level l+1 to level l) and bc = P^T rf */
+static void semi_prolong(const orc_prec *P, int l, const double *ec, double *ef)
+{
+    int sx = P->sx[l], sxc = P->sx[l + 1], m = P->m;
+    for (int J = 1; J <= m; J++)
+        for (int I = 1; I <= sx; I++) {
+            int Ic[2];
+            double w[2];
+            int c = semi_pcols(P, l, I, J, Ic, w);
+            for (int t = 0; t < c; t++) ef[(size_t)(J - 1) * sx + (I - 1)] += w[t] * ec[(size_t)(J - 1) * sxc + (Ic[t] - 1)];
+        }
+}
+static void semi_restrict(const orc_prec *P, int l, const double *rf, double *bc)
+{
+    int sx = P->sx[l], sxc = P->sx[l + 1], m = P->m;
+    for (size_t k = 0; k < (size_t)sxc * m; k++) bc[k] = 0.0;
+    for (int J = 1; J <= m; J++)
+        for (int I = 1; I <= sx; I++) {
+            int Ic[2];
+            double w[2];
+            int c = semi_pcols(P, l, I, J, Ic, w);
+            for (int t = 0; t < c; t++) bc[(size_t)(J - 1) * sxc + (Ic[t] - 1)] += w[t] * rf[(size_t)(J - 1) * sx + (I - 1)];
+        }
+}
+
+static void semi_vcycle(orc_prec *P, int l, const double *b, double *e)
+{
+    if (l == P->snlev - 1) {
+        for (int s = 0; s < 4; s++) orc_semi_gs(P, l, b, e);
+        return;
+    }
+    size_t nl = (size_t)P->sx[l] * P->m, nc = (size_t)P->sx[l + 1] * P->m;
+    double *r = P->sr[l], *bc = P->sb[l + 1], *ec = P->se[l + 1];
+    orc_semi_gs(P, l, b, e);
+    semi_apply(P, l, e, r);
+    for (size_t k = 0; k < nl; k++) r[k] = b[k] - r[k];
+    semi_restrict(P, l, r, bc);
+    for (size_t k = 0; k < nc; k++) ec[k] = 0.0;
+    semi_vcycle(P, l + 1, bc, ec);
+    semi_prolong(P, l, ec, e);
+    orc_semi_gs(P, l, b, e);
+}
+
+static int semi_corner_solve(orc_prec *P, const double *b, double *e)
+{
+    int m = P->m;
+    size_t nc = (size_t)m * m;
+    double *bs = dalloc(nc), *r = dalloc(nc);
+    for (size_t k = 0; k < nc; k++) { bs[k] = P->LD[0][k] * b[k]; e[k] = 0.0; }
+    double b0 = nrm2(nc, bs);
+    int cyc = 0;
+    while (b0 > 0.0) {
+        if (P->fixed_cycles > 0 ? cyc >= P->fixed_cycles : cyc >= P->max_cycles) break;
+        semi_vcycle(P, 0, bs, e);
+        cyc++;
+        if (P->fixed_cycles <= 0) {
+            semi_apply(P, 0, e, r);
+            for (size_t k = 0; k < nc; k++) r[k] = bs[k] - r[k];
+            if (nrm2(nc, r) <= b0 / P->reduction) break;
+        }
+    }
+    free(bs); free(r);
+    return cyc;
+}
+
+/* level data of the parabolic cycle, for the tests: the nine planes of A_l
+ * (9 * width * m values, plane (dy+1)*3 + (dx+1)) and, below the coarsest
+ * level, the interpolation weights of the odd columns (0 elsewhere) */
+int orc_semi_nlev(const orc_prec *P) { return P->semi ? P->snlev : 0; }
+int orc_semi_width(const orc_prec *P, int l) { return P->sx[l]; }
+void orc_semi_level(const orc_prec *P, int l, double *A9, double *PW, double *PE)
+{
+    size_t n = (size_t)P->sx[l] * P->m;
+    memcpy(A9, P->A9[l], 9 * n * sizeof(double));
+    if (l < P->snlev - 1) { memcpy(PW, P->PW[l], n * sizeof(double)); memcpy(PE, P->PE[l], n * sizeof(double)); }
+}
+
 /* M_CC^{-1} b (or M_CC^{-T} b): stationary multigrid iteration from e = 0.
  * Returns the number of cycles taken. */
 int orc_corner_solve(orc_prec *P, const double *b, double *e, int transpose)
@@ -527,6 +775,7 @@ int orc_corner_solve(orc_prec *P, const double *b, double *e, int transpose)
     int m = P->m;
     size_t nc = (size_t)m * m;
     for (size_t k = 0; k < nc; k++) e[k] = 0.0;
+    if (P->semi) return transpose ? -1 : semi_corner_solve(P, b, e);
     if (P->corner_exact) {
         /* the idealised M-hat of Sec. 3.1: exact A_CC solve (banded LU on the
          * corner block, which is the level-0 operator) */
