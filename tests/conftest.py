@@ -30,3 +30,26 @@ def read_table(name):
                 continue
             rows[parts[0]] = [None if p == "-" else float(p) for p in parts[1:]]
     return header, rows
+
+
+def first_cycle_estimate_count(N, A, f, P, target, kmax=12):
+    """Iteration at which the least-squares residual estimate of the first
+    FGMRES cycle (MGS Arnoldi on the oracle's A, right-preconditioned with
+    the oracle's P, zero initial guess) meets the target, or None."""
+    import numpy as np
+    import oracle
+    beta = np.linalg.norm(f)
+    V, H = [f / beta], np.zeros((kmax + 1, kmax))
+    for j in range(kmax):
+        w = oracle.apply(N, A, P.apply(V[j])[0])
+        for i in range(j + 1):
+            H[i, j] = w @ V[i]
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        V.append(w / H[j + 1, j])
+        e1 = np.zeros(j + 2)
+        e1[0] = beta
+        y = np.linalg.lstsq(H[: j + 2, : j + 1], e1, rcond=None)[0]
+        if np.linalg.norm(e1 - H[: j + 2, : j + 1] @ y) <= target:
+            return j + 1
+    return None

@@ -22,7 +22,7 @@ import pytest
 from scipy.linalg import solve_triangular
 
 import oracle
-from tests.conftest import read_table
+from tests.conftest import first_cycle_estimate_count, read_table
 from tests.test_oracle_discretization import mms_problem
 
 
@@ -112,26 +112,6 @@ def test_relaxation_is_downstream_gauss_seidel():
     e_ref = np.empty(m * w)
     e_ref[order] = solve_triangular(L, b[order] - (Ap - L) @ e0[order], lower=True)
     np.testing.assert_allclose(P.semi_gs(1, b, e0), e_ref, rtol=1e-11, atol=1e-12 * np.abs(e_ref).max())
-
-
-def first_cycle_estimate_count(N, A, f, P, target, kmax=12):
-    """Iteration at which the least-squares residual estimate of the first
-    FGMRES cycle (MGS Arnoldi on A, zero initial guess) meets the target."""
-    beta = np.linalg.norm(f)
-    V, H = [f / beta], np.zeros((kmax + 1, kmax))
-    for j in range(kmax):
-        w = oracle.apply(N, A, P.apply(V[j])[0])
-        for i in range(j + 1):
-            H[i, j] = w @ V[i]
-            w = w - H[i, j] * V[i]
-        H[j + 1, j] = np.linalg.norm(w)
-        V.append(w / H[j + 1, j])
-        e1 = np.zeros(j + 2)
-        e1[0] = beta
-        y = np.linalg.lstsq(H[: j + 2, : j + 1], e1, rcond=None)[0]
-        if np.linalg.norm(e1 - H[: j + 2, : j + 1] @ y) <= target:
-            return j + 1
-    return None
 
 
 def test_parabolic_iterations_and_cycles_match_paper_table():
