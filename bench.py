@@ -341,7 +341,8 @@ def roofline(classes):
     c = classes[dom]
     achieved = c["GBps"] or 0.0
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+            "frac": round(achieved / peak, 4),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback (6.8 TB/s)",
             "traffic": ncu_traffic(dom), "share": c["share"],
             "note": "achieved = algorithmic bytes / CUDA-event device time of every launch of the class "
                     "in an instrumented replay of one step"}
