@@ -9,8 +9,9 @@ pinned against what fixes it independently of its code:
   from the block's edges) sum to one, so constants are interpolated exactly;
 * a relaxation sweep equals the textbook Gauss-Seidel step in the downstream
   order, a triangular solve;
-* the paper's counts: 3 V-cycles per corner solve, and the FGMRES iteration
-  counts of Table tab:parabolic_times_iters at N = 128, 256, 512.  Ten of
+* the paper's counts: 3 V-cycles per corner solve, the FGMRES iteration
+  counts of Table tab:parabolic_times_iters at N = 128, 256, 512, and the
+  errors of tab:parabolic_errors for the iterates it stops at (1%).  Ten of
   the twelve match the oracle's count exactly.  At eps = 1e-8, N = 256 and
   512 the paper's 4 is the iteration at which FGMRES's least-squares
   residual estimate meets the target; the true residual of that iterate is
@@ -115,16 +116,21 @@ def test_relaxation_is_downstream_gauss_seidel():
 
 
 def test_parabolic_iterations_and_cycles_match_paper_table():
+    """Also tab:parabolic_errors: the error of the iterate the algorithm stops
+    at is the table's within 1% (as for the exact discrete solution)."""
     header, rows = read_table("table_parabolic_iterations.txt")
+    _, err_rows = read_table("table_parabolic_errors.txt")
     for eps_s, vals in rows.items():
         eps = float(eps_s)
-        for N, ref in zip((128, 256, 512), vals[:3]):
+        errs = err_rows[eps_s]
+        for N, ref, ref_err in zip((128, 256, 512), vals[:3], errs[:3]):
             x, y, c1, c2, r, f, ue = mms_problem("par", N, eps)
             P = oracle.Prec(N, eps, x, y, c1, c2, r, reduction=1e2, parabolic=True)
             A = oracle.assemble(N, eps, x, y, c1, c2, r)
             target = 10 * np.log(N) / N
             u, st, it, rr, mc = oracle.fgmres(N, A, f, P, tol=target, tol_abs=True, scaled=False)
             assert st == 0 and mc == 3, (eps, N, mc)           # "only 3 V-cycles"
+            assert abs(np.abs(u - ue).max() - ref_err) <= 0.01 * ref_err, (eps, N)
             if eps == 1e-8 and N >= 256:
                 assert it == 6 and first_cycle_estimate_count(N, A, f, P, target) == int(ref), (eps, N, it)
             else:
