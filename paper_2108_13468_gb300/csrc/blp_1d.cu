@@ -3,8 +3,10 @@
 // Each problem is -eps u'' - c(x) u' + r(x) u = f on (0,1), u(0) = u(1) = 0
 // (eq. 1D), discretised by the upwind scheme of eq. (stencil_1d) on the
 // Shishkin mesh of eq. (tau 1D) (q = 1/2: N/2 intervals on [0, tau]), and
-// solved by GMRES without restarts, right-preconditioned with M of
-// eq. (block_M), stopping on the true residual ||f - A u||_inf (Sec. 2.5.1).
+// solved by GMRES without restarts on the left-preconditioned system
+// M^-1 A u = M^-1 f, M of eq. (block_M), stopping on the true residual
+// ||f - A u||_inf (Sec. 2.5.1).  Left preconditioning is the setting of the
+// paper's Table 2 (MATLAB's gmres preconditions on the left).
 //
 // A 1D problem is a tridiagonal system of at most a few thousand unknowns:
 // far too small to spread over the GPU.  The batch is what fills it: one
@@ -94,24 +96,25 @@ __global__ void k_gmres_1d(blp_1d_problem *P, const long long *off, double *ws, 
     }
     const Tri1D A{n, NL, sub, dia, sup, cp, rp};
 
-    // GMRES from u = 0: r_0 = f
+    // GMRES from u = 0 on M^-1 A u = M^-1 f: the true residual of u = 0 is f,
+    // the Krylov space starts at M^-1 f
     double beta = 0.0, res = 0.0;
     for (int q = 0; q < n; q++) {
-        beta += p.f[q] * p.f[q];
         res = fmax(res, fabs(p.f[q]));
         x[q] = 0.0;
     }
-    beta = sqrt(beta);
     int it = 0, status = BLP_ERR_NOCONV;
     if (res <= p.stop) {
         status = BLP_OK;
     } else {
-        for (int q = 0; q < n; q++) V[q] = p.f[q] / beta;
+        A.precond(p.f, z);
+        beta = sqrt(dot(z, z, n));
+        for (int q = 0; q < n; q++) V[q] = z[q] / beta;
         g[0] = beta;
         for (int j = 0; j < m; j++) {
             double *Hj = H + (long long)j * (m + 1);
-            A.precond(V + (long long)j * n, z);
-            A.matvec(z, w);
+            A.matvec(V + (long long)j * n, t);
+            A.precond(t, w);
             for (int i = 0; i <= j; i++) {   // modified Gram-Schmidt
                 const double *Vi = V + (long long)i * n;
                 const double hij = dot(w, Vi, n);
@@ -142,13 +145,12 @@ __global__ void k_gmres_1d(blp_1d_problem *P, const long long *off, double *ws, 
                 for (int l = i + 1; l <= j; l++) s -= H[(long long)l * (m + 1) + i] * y[l];
                 y[i] = H[(long long)i * (m + 1) + i] != 0.0 ? s / H[(long long)i * (m + 1) + i] : 0.0;
             }
-            // iterate u = M^-1 V y and its true residual (the stopping rule of Sec. 2.5.1)
-            for (int q = 0; q < n; q++) t[q] = 0.0;
+            // iterate u = V y and its true residual (the stopping rule of Sec. 2.5.1)
+            for (int q = 0; q < n; q++) x[q] = 0.0;
             for (int i = 0; i <= j; i++) {
                 const double *Vi = V + (long long)i * n;
-                for (int q = 0; q < n; q++) t[q] += y[i] * Vi[q];
+                for (int q = 0; q < n; q++) x[q] += y[i] * Vi[q];
             }
-            A.precond(t, x);
             A.matvec(x, w);
             res = 0.0;
             for (int q = 0; q < n; q++) res = fmax(res, fabs(p.f[q] - w[q]));
