@@ -15,8 +15,6 @@
 
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/blp.h"
 
 namespace {
@@ -27,7 +25,6 @@ namespace {
 // every call; only the ticket must start at zero, and each call clears it.
 constexpr int kRows = 8;
 constexpr int kScratchDoubles = kRows + 4 * BLP_NOALLOC_MAX_N;  // 256 KiB + 64 B
-constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;
 
 static __device__ __align__(256) double blp_noalloc_scratch[kScratchDoubles];
@@ -114,31 +111,31 @@ __global__ void __launch_bounds__(kThreads) k_residual_noalloc(int N, const doub
     }
 }
 
-std::mutex g_mu;
-double *g_scratch[kMaxDevices];
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on each device does it).
+// Device address of the scratch array on the current device.  It is looked
+// up on every call: the lookup is cheap, and a cached address would go stale
+// if the caller reset the device (cudaDeviceReset) and the module were
+// loaded again.  The first lookup on a device loads this module there, which
+// is when the array is reserved.
 int scratch_address(double **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BLP_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, blp_noalloc_scratch) != cudaSuccess || !p) return BLP_ERR_CUDA;
-        g_scratch[dev] = static_cast<double *>(p);
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, blp_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return BLP_ERR_CUDA;
     }
-    *out = g_scratch[dev];
+    *out = static_cast<double *>(p);
     return BLP_OK;
 }
 
-bool on_device(const void *p) {
+// True for managed memory and for device memory of the current device.  A
+// device pointer of another GPU is refused: the kernel runs on the current
+// device and would read memory it cannot reach.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 }  // namespace
@@ -148,10 +145,12 @@ extern "C" int blp_residual_noalloc(int N, const double *x, const double *y, dou
                                     double *res, double *norms, void *stream) {
     if (N < 8 || N % 2 != 0 || N > BLP_NOALLOC_MAX_N) return BLP_ERR_ARG;
     if (!(eps > 0.0 && eps <= 1.0)) return BLP_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BLP_ERR_CUDA;
     const void *in[] = {x, y, c1, c2, r, f, u};
     for (const void *p : in)
-        if (!p || !on_device(p)) return BLP_ERR_ARG;
-    if (res && !on_device(res)) return BLP_ERR_ARG;
+        if (!p || !on_device(p, dev)) return BLP_ERR_ARG;
+    if (res && !on_device(res, dev)) return BLP_ERR_ARG;
     double *scratch = nullptr;
     int st = scratch_address(&scratch);
     if (st != BLP_OK) return st;
