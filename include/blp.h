@@ -66,11 +66,24 @@ typedef struct {
     int corner_max_cycles;     /* cap on corner cycles per application (default 50) */
     int corner_fixed_cycles;   /* >0: exactly this many corner cycles (M becomes a fixed linear map) */
     int check_coefficients;    /* nonzero: blp_setup validates c1, c2, r (default 1) */
-    int mesh;                  /* BLP_MESH_SHISHKIN (default) or BLP_MESH_GRADED (see blp_mesh_graded) */
+    int mesh;                  /* BLP_MESH_SHISHKIN (default), BLP_MESH_GRADED or BLP_MESH_PARABOLIC */
 } blp_params;
 
 #define BLP_MESH_SHISHKIN 0    /* piecewise-uniform layer mesh (blp_mesh) */
 #define BLP_MESH_GRADED 1      /* graded layer mesh, same tau and split (blp_mesh_graded) */
+/* One parabolic and one exponential layer (Sec. 3, eq. (tau parabolic);
+ * Sec. 3.2, first case): blp_mesh in x (beta_x = C_low), blp_mesh_parabolic
+ * in y (beta_y is not used; c2 >= 0 is required instead of c2 >= beta_y), the
+ * blocks M_II, M_YY, M_XX of Sec. 3.1 unchanged, and the corner block
+ * approximated by the semicoarsening cycle of Sec. 3.2: rows rescaled by
+ * hb_i kb_j, coarsening by 2 in x only, operator-induced interpolation from
+ * the North-South collapsed stencil, restriction P^T, Galerkin (nine-point)
+ * coarse operators, downstream point Gauss-Seidel, V(1,1), four coarsest
+ * sweeps, cycles until the scaled corner residual falls by corner_reduction
+ * (the paper takes 1e2 for this case).  Forward solves and forward
+ * preconditioner applications only: blp_solve_adjoint and transposed
+ * applications return BLP_ERR_ARG on such a handle. */
+#define BLP_MESH_PARABOLIC 2
 
 /* Statistics of the last solve. */
 typedef struct {
@@ -107,6 +120,13 @@ double blp_mesh(int N, double eps, double sigma, double beta, double *x);
  * (coarse nodes at even fine indices, transfer weights 1/2 and 1/4) are
  * unchanged on this mesh. */
 double blp_mesh_graded(int N, double eps, double sigma, double beta, double *x);
+
+/* Parabolic-layer mesh (Sec. 3, eq. (tau parabolic)), the y mesh of
+ * BLP_MESH_PARABOLIC: tau = min(1/2, sigma sqrt(eps) ln(N)), N/2 equal
+ * intervals on [0,tau] and on [tau,1], nodes by the rule of blp_mesh.
+ * x: host array of N+1 doubles (caller-owned).  Returns tau, or a negative
+ * value for invalid arguments. */
+double blp_mesh_parabolic(int N, double eps, double sigma, double *x);
 
 /* Assemble the operator (Sec. 3 stencil) and build the preconditioner
  * (Sec. 3.1 blocks, line factorisations, Sec. 3.2 corner hierarchy) on the
@@ -232,10 +252,11 @@ int blp_solve_batched_tuned(blp_batch_item *items, int count, int concurrency);
  * discretised by the upwind scheme of eq. (stencil_1d) on the Shishkin mesh
  * of eq. (tau 1D) with tau = min(1/2, sigma eps ln(N) / c_low) and N/2
  * intervals on each side of tau, and solved by GMRES without restarts from
- * u = 0, right-preconditioned with M of eq. (block_M) (A on the layer block
- * and both coupling entries, the upper triangle of the interior block),
- * stopping at the first iterate with ||f - A u||_inf <= stop (the rule of
- * Sec. 2.5.1 with K g(N) = stop), or after maxit iterations.
+ * u = 0 on the left-preconditioned system M^-1 A u = M^-1 f, M of
+ * eq. (block_M) (A on the layer block and both coupling entries, the upper
+ * triangle of the interior block), the setting of Table 2, stopping at the
+ * first iterate with ||f - A u||_inf <= stop (the rule of Sec. 2.5.1 with
+ * K g(N) = stop), or after maxit iterations.
  *   N        intervals, even, 8 <= N <= BLP_1D_MAX_N
  *   c, r, f  DEVICE (or managed) arrays of N-1 values at the interior nodes
  *            x_1 .. x_{N-1} of that mesh (caller-owned, read only)
@@ -285,19 +306,25 @@ int blp_solve_1d_batched(blp_1d_problem *probs, int count, void *stream);
  * fields c1, c2, r, and writes
  *     norms[0] = ||s||_2,        norms[1] = ||D^-1 s||_2,
  *     norms[2] = ||f||_2,        norms[3] = ||D^-1 f||_2     (D = diag(A)).
- * x, y, c1, c2, r, f, u: DEVICE (or managed) arrays, read only; fields have
- * (N-1)^2 entries in the layout of the other calls.  res: device array of
- * (N-1)^2 doubles receiving s, or NULL.  norms: 4 doubles, host or device,
- * or NULL.  stream: a cudaStream_t (NULL: legacy default stream); the call
- * returns after its work on that stream has completed.
+ * x, y, c1, c2, r, f, u: arrays in the current device's memory (or managed
+ * memory), read only; fields have (N-1)^2 entries in the layout of the other
+ * calls.  res: such an array of (N-1)^2 doubles receiving s, or NULL (the
+ * norms are still computed).  norms: 4 doubles, host or device, or NULL.
+ * stream: a cudaStream_t of the current device (NULL: legacy default
+ * stream); the call returns after its work on that stream has completed.
  * Errors: BLP_ERR_ARG for N odd, N < 8, N > BLP_NOALLOC_MAX_N, eps outside
- * (0,1], or a null or host input array; BLP_ERR_CUDA when a CUDA call fails.
+ * (0,1], or a null input array, a host array or another GPU's array;
+ * BLP_ERR_CUDA when a CUDA call fails.
  * Memory: reduction partials live in one fixed device array per device
- * (BLP_NOALLOC_MAX_N bounds its size).  Its address is looked up on the
- * first call on each device, so make that first call before any stream
- * capture begins.  Every call on a device shares that array, so calls whose
- * GPU work overlaps (different streams, or several host threads) race:
- * serialise them. */
+ * (BLP_NOALLOC_MAX_N bounds its size), held by every GPU that loads the
+ * library until the process exits.  Each call looks up that array's device
+ * address with the caller's device current.  The first call on a device also
+ * loads this code onto the device, which is when the array is reserved: make
+ * that first call during set-up, before device memory is fully reserved and
+ * before any stream capture begins.  Every call on a device shares the array
+ * and each call clears what must start at zero, so calls whose GPU work
+ * overlaps (different streams, or several host threads) race: serialise
+ * them. */
 int blp_residual_noalloc(int N, const double *x, const double *y, double eps, const double *c1,
                          const double *c2, const double *r, const double *f, const double *u,
                          double *res, double *norms, void *stream);

@@ -21,11 +21,12 @@ import ctypes
 import numpy as np
 
 from . import _native as N_
-from ._native import (BLP_FP64, BLP_MESH_GRADED, BLP_MESH_SHISHKIN, BLP_MIXED, BLP_STOP_ABS2, BLP_STOP_REL2,
-                      BLP_STOP_SCALED, BlpError, Info, Params)
+from ._native import (BLP_FP64, BLP_MESH_GRADED, BLP_MESH_PARABOLIC, BLP_MESH_SHISHKIN, BLP_MIXED, BLP_STOP_ABS2,
+                      BLP_STOP_REL2, BLP_STOP_SCALED, BlpError, Info, Params)
 
 __all__ = ["mesh", "Solver", "Params", "Info", "BlpError", "BLP_FP64", "BLP_MIXED", "BLP_STOP_SCALED",
-           "BLP_STOP_REL2", "BLP_STOP_ABS2", "BLP_MESH_SHISHKIN", "BLP_MESH_GRADED", "default_params", "solve",
+           "BLP_STOP_REL2", "BLP_STOP_ABS2", "BLP_MESH_SHISHKIN", "BLP_MESH_GRADED", "BLP_MESH_PARABOLIC", "default_params",
+           "solve",
            "solve_batched", "solve_1d_batched", "residual_noalloc"]
 
 
@@ -39,14 +40,22 @@ def default_params(**kw) -> Params:
     return p
 
 
-def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, graded: bool = False):
+def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, graded: bool = False, parabolic: bool = False):
     """Shishkin mesh nodes x[0..N] (blp_mesh) and the transition point tau;
-    graded=True: the graded layer mesh with the same tau (blp_mesh_graded)."""
+    graded=True: the graded layer mesh with the same tau (blp_mesh_graded);
+    parabolic=True: the parabolic-layer mesh, tau = min(1/2, sigma sqrt(eps)
+    ln N) (blp_mesh_parabolic; beta is not used)."""
+    if graded and parabolic:
+        raise ValueError("graded and parabolic are exclusive")
     x = np.zeros(N + 1)
-    fn = N_.load().blp_mesh_graded if graded else N_.load().blp_mesh
-    tau = fn(N, eps, sigma, beta, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    xp = x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if parabolic:
+        name, tau = "blp_mesh_parabolic", N_.load().blp_mesh_parabolic(N, eps, sigma, xp)
+    else:
+        name = "blp_mesh_graded" if graded else "blp_mesh"
+        tau = getattr(N_.load(), name)(N, eps, sigma, beta, xp)
     if tau < 0:
-        raise BlpError(N_.BLP_ERR_ARG, "blp_mesh_graded" if graded else "blp_mesh")
+        raise BlpError(N_.BLP_ERR_ARG, name)
     return x, tau
 
 
@@ -225,7 +234,7 @@ def solve_batched(problems, tol=1e-10, concurrency=8, autotune=False):
 
 def solve_1d_batched(problems, stream=None):
     """blp_solve_1d_batched: the 1D method of Sec. 2 (upwind scheme, Shishkin
-    mesh, GMRES right-preconditioned with M of eq. (block_M), true-residual
+    mesh, GMRES left-preconditioned with M of eq. (block_M), true-residual
     stop) for many problems at once, one GPU thread per problem.
 
     problems: dicts with N, eps, stop (absolute ||f - A u||_inf target) and
@@ -293,7 +302,9 @@ def residual_noalloc(N, x, y, eps, c1, c2, r, f, u, res=None, stream=None):
     return norms
 
 
-def solve(f, c1, c2, r, N, eps, tol=1e-10, **params):
-    """Differentiable solve u = A(c1, c2, r)^{-1} f (see autograd.BLPSolve)."""
+def solve(f, c1, c2, r, N, eps, tol=1e-10, adjoint_tol=None, **params):
+    """Differentiable solve u = A(c1, c2, r)^{-1} f (see autograd.BLPSolve).
+    tol: forward tolerance; adjoint_tol: tolerance of the adjoint solve in the
+    backward pass (default: tol)."""
     from .autograd import BLPSolve
-    return BLPSolve.apply(f, c1, c2, r, N, eps, tol, params)
+    return BLPSolve.apply(f, c1, c2, r, N, eps, tol, adjoint_tol, params)

@@ -15,7 +15,7 @@ BLP_OK, BLP_ERR_ARG, BLP_ERR_COEF, BLP_ERR_NOCONV, BLP_ERR_TIMEOUT, BLP_ERR_CUDA
 BLP_FP64, BLP_MIXED = 0, 1
 BLP_STOP_SCALED, BLP_STOP_REL2, BLP_STOP_ABS2 = 0, 1, 2
 BLP_NOALLOC_MAX_N = 8192
-BLP_MESH_SHISHKIN, BLP_MESH_GRADED = 0, 1
+BLP_MESH_SHISHKIN, BLP_MESH_GRADED, BLP_MESH_PARABOLIC = 0, 1, 2
 BLP_1D_MAX_N, BLP_1D_MAXIT = 65536, 128
 
 c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
@@ -61,6 +61,7 @@ SIGNATURES = {
     "blp_params_default": (None, [ctypes.POINTER(Params)]),
     "blp_mesh": (c_double, [c_int, c_double, c_double, c_double, _DP]),
     "blp_mesh_graded": (c_double, [c_int, c_double, c_double, c_double, _DP]),
+    "blp_mesh_parabolic": (c_double, [c_int, c_double, c_double, _DP]),
     "blp_setup": (c_int, [ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]),
     "blp_set_stream": (c_int, [c_void_p, c_void_p]),
     "blp_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(Info)]),

@@ -14,7 +14,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libblp.so")
-SOURCES = ["blp_setup.cu", "blp_precond.cu", "blp_krylov.cu", "blp_noalloc.cu", "blp_batch.cu", "blp_tune.cu", "blp_1d.cu"]
+SOURCES = ["blp_setup.cu", "blp_precond.cu", "blp_krylov.cu", "blp_noalloc.cu", "blp_batch.cu", "blp_tune.cu", "blp_1d.cu", "blp_semi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -181,6 +181,31 @@ struct Hierarchy {
     Level<T> lev[BLP_MAXLEV];
 };
 
+// One level of the corner cycle for one parabolic and one exponential layer
+// (Sec. 3.2): x-semicoarsened, width sx (columns) by m = N/2 (rows), with a
+// nine-point operator.  Natural arrays are row-major (row J-1, column I-1).
+// The Gauss-Seidel sweep reads its per-node data in a SKEW order: rows in
+// blocks of 32 (block kb = (m - J) / 32, lane = (m - J) % 32), and node
+// (I, J) of a block at step s = (sx - I) + 2 lane, slot (kb S + s) 32 + lane,
+// S = sx + 62 steps per block; slots of no node are zero.
+template <typename T>
+struct SemiLev {
+    int sx = 0, m = 0;
+    int S = 0, nb = 0;              // steps per 32-row block, blocks
+    long long nskew = 0;            // skew slots
+    T *A9 = nullptr;                // 9 planes of sx*m, plane (dy+1)*3 + (dx+1): entry to (I+dx, J+dy)
+    T *gE = nullptr, *gN = nullptr, *gNE = nullptr, *gNW = nullptr;   // skew: chain couplings a/aC
+    T *c0 = nullptr;                // skew: sweep right-hand side, (b - old-value terms) / aC
+    T *PW = nullptr, *PE = nullptr; // natural: interpolation weights of the odd columns from level l+1
+    T *b = nullptr, *e = nullptr;   // natural
+};
+
+template <typename T>
+struct SemiHier {
+    int nlev = 0;
+    SemiLev<T> lev[BLP_MAXLEV];
+};
+
 struct DevState {       // device scalars of the solver (double)
     double red[8];      // reduction results
     int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[3]: running max of cycles
@@ -227,6 +252,10 @@ struct blp_handle {
     Coefs<float> cf;
     Hierarchy<double> hd;
     Hierarchy<float> hf;
+    // parabolic-layer corner cycle (mesh == BLP_MESH_PARABOLIC): semicoarsened levels
+    bool semi = false;
+    SemiHier<double> sd;
+    SemiHier<float> sf;
     // reduction scratch
     double *partials = nullptr;     // [BLP_RED_BLOCKS * BLP_PART_STRIDE + 64]
     DevState *dev = nullptr;
@@ -266,6 +295,14 @@ struct blp_handle {
 // Stream-ordered device allocation from the library pool (handle's stream).
 int blp_internal_alloc(blp_handle *h, void **p, size_t bytes);
 void blp_internal_free(blp_handle *h, void *p);
+// Build the semicoarsened corner hierarchy of the parabolic-layer case from
+// level 0 of the full-coarsening hierarchy (setup).
+int blp_internal_semi_build(blp_handle *h);
+void blp_internal_semi_free(blp_handle *h);
+// M_CC^-1 b0 by the semicoarsening cycle (forward only): b0 in the corner
+// level's skew layout (row-normalised right-hand side), the result written to
+// out (corner region of a region-major vector, padding set to zero).
+template <typename T> int semi_corner_solve(blp_handle *h, const T *b0, T *out, int *cycles);
 // Precompute the line-chain scan multipliers of both precisions (setup).
 int blp_internal_chain_pre(blp_handle *h);
 // blp_setup with the handle's work issued on `stream` from the start.

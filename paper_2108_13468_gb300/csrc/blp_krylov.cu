@@ -651,6 +651,7 @@ extern "C" int blp_solve(blp_handle *h, const double *f, double *u, double tol, 
     return solve_on_capturable_stream(h, f, u, tol, info, 0);
 }
 extern "C" int blp_solve_adjoint(blp_handle *h, const double *g, double *lambda, double tol, blp_info *info) {
+    if (h && h->semi) return BLP_ERR_ARG;   // the parabolic-layer corner cycle is forward only
     return solve_on_capturable_stream(h, g, lambda, tol, info, 1);
 }
 

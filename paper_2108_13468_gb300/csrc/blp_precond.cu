@@ -683,7 +683,13 @@ __global__ void k_corner_norm(Level<T> Lv, const T *__restrict__ b, const T *__r
 
 // mode 0: red[0] = ||b||^2 / reduction^2, flags[0] = (||b|| == 0), flags[1] = 0
 // mode 1: flags[1]++, flags[0] = (||r||^2 <= red[0]) or cycles reached the cap
-__global__ void k_corner_finish(double *partials, int nb, DevState *st, int mode, double red2, int maxc) {
+// stall2 > 0 (FP32 iterations): also stop once a cycle leaves ||r||^2 above
+// stall2 times the previous cycle's (red[2]).  An FP32 iterate's residual has
+// a rounding floor near 2^-24 || |A| |e| ||, which on a fine, diffusion-
+// dominated corner (eps N >> 1) lies above the 1e3 reduction; the V-cycle
+// contracts by far more than stall2 per cycle until it reaches that floor.
+__global__ void k_corner_finish(double *partials, int nb, DevState *st, int mode, double red2, int maxc,
+                                double stall2) {
     if (st->flags[0] && mode == 1) return;
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) s += partials[i];
@@ -695,10 +701,14 @@ __global__ void k_corner_finish(double *partials, int nb, DevState *st, int mode
             st->flags[1] = 0;
         } else {
             st->flags[1] += 1;
-            if (s <= st->red[0] || st->flags[1] >= maxc) st->flags[0] = 1;
+            if (s <= st->red[0] || st->flags[1] >= maxc || (stall2 > 0.0 && s > stall2 * st->red[2])) st->flags[0] = 1;
         }
+        st->red[2] = s;
     }
 }
+
+// the FP32 corner iteration stops when a cycle fails to halve the residual
+template <typename T> constexpr double corner_stall2() { return sizeof(T) == 4 ? 0.25 : 0.0; }
 
 // ---------------------------------------------------------------------------
 // Fused coarse levels (Sec. 3.2 cycle below a size where a level fits in
@@ -1090,7 +1100,8 @@ static int corner_more(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int cou
         ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 7 * sizeof(T));
         k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[cy.cur[0]], 1, h->partials, done);
         LAUNCH_CHECK(h);
-        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles);
+        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles,
+                                                 corner_stall2<T>());
         LAUNCH_CHECK(h);
     }
     return BLP_OK;
@@ -1111,7 +1122,8 @@ static int corner_front(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int ba
         ProfScope ps(h, KC_CORNER_NORM, (double)L0.R.mx * L0.R.my * 2 * sizeof(T));
         k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
         LAUNCH_CHECK(h);
-        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles);
+        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles,
+                                                 corner_stall2<T>());
         LAUNCH_CHECK(h);
     }
     cy.skip = done;
@@ -1295,8 +1307,9 @@ static int precond_graph(blp_handle *h, const T *v_in, T *z_out, int trans, int 
 template <typename T>
 int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles) {
     const int prec = sizeof(T) == 4 ? 1 : 0;
+    if (h->semi && trans) return BLP_ERR_ARG;   // the parabolic-layer corner cycle is forward only
     if (h->use_graphs && h->warm[prec][trans ? 1 : 0] && h->stream != 0 && !h->prof.on &&
-        h->p.corner_fixed_cycles <= 0 && coarse_start(hier_of<T>(h)) > 0)
+        h->p.corner_fixed_cycles <= 0 && coarse_start(hier_of<T>(h)) > 0 && !h->semi)
         return precond_graph<T>(h, v, z, trans, cycles);
     h->warm[prec][trans ? 1 : 0] = true;   // the first application runs eagerly (kernel attributes set outside any capture)
     Coefs<T> &c = coefs_of<T>(h);
@@ -1319,6 +1332,7 @@ int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles) {
             k_corner_rhs<T><<<grid_for(C.size, 256), 256, 0, h->stream>>>(lay, v, z, c.wE, c.wN, b0, nullptr);
             LAUNCH_CHECK(h);
         }
+        if (h->semi) return semi_corner_solve<T>(h, b0, z + C.off, cycles);   // Sec. 3.2, parabolic case
         T *e = nullptr;
         if ((rc = corner_solve<T, false>(h, b0, &e, cycles))) return rc;
         {

@@ -35,6 +35,20 @@ extern "C" double blp_mesh_graded(int N, double eps, double sigma, double beta, 
     return tau;
 }
 
+// Parabolic-layer mesh in y (Sec. 3, eq. (tau parabolic)): tau = min(1/2,
+// sigma sqrt(eps) ln N), N/2 equal intervals on each side of tau.
+extern "C" double blp_mesh_parabolic(int N, double eps, double sigma, double *x) {
+    if (N < 8 || (N & 1) || !(eps > 0.0) || eps > 1.0 || !(sigma > 0.0) || !x) return -1.0;
+    double tau = sigma * std::sqrt(eps) * std::log((double)N);
+    if (tau > 0.5) tau = 0.5;
+    const int m = N / 2;
+    for (int i = 0; i <= m; i++) x[i] = ((double)i / (double)m) * tau;
+    for (int i = m + 1; i <= N; i++) x[i] = tau + ((double)(i - m) / (double)m) * (1.0 - tau);
+    x[0] = 0.0;
+    x[N] = 1.0;
+    return tau;
+}
+
 extern "C" void blp_params_default(blp_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
@@ -360,6 +374,7 @@ extern "C" void blp_destroy(blp_handle *h) {
     free_coefs(h, h->cf);
     free_hier(h, h->hd);
     free_hier(h, h->hf);
+    blp_internal_semi_free(h);
     blp_internal_prof_flush(h);
     for (auto &e : h->prof.ev) cudaEventDestroy(e);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
@@ -589,7 +604,8 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
     h->hy.resize(N + 1);
     auto mesh = p.mesh == BLP_MESH_GRADED ? blp_mesh_graded : blp_mesh;
     h->tau_x = mesh(N, p.eps, p.sigma, p.beta_x, h->hx.data());
-    h->tau_y = mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
+    h->tau_y = p.mesh == BLP_MESH_PARABOLIC ? blp_mesh_parabolic(N, p.eps, p.sigma, h->hy.data())
+                                            : mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
     TRY(dalloc(h, &h->x, N + 1));
     TRY(dalloc(h, &h->y, N + 1));
     CUDA_TRY(cudaMemcpyAsync(h->x, h->hx.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice, h->stream));
@@ -612,7 +628,9 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
         int nb = 128;
         double *out = h->partials;
         int *nf = h->err + 1;
-        k_check_coefs<<<nb, 256, 0, h->stream>>>(h->c1, h->c2, h->r, n, p.beta_x, p.beta_y, out, nf);
+        // parabolic case: no convection in y is required (c2 >= 0)
+        const double by = p.mesh == BLP_MESH_PARABOLIC ? 0.0 : p.beta_y;
+        k_check_coefs<<<nb, 256, 0, h->stream>>>(h->c1, h->c2, h->r, n, p.beta_x, by, out, nf);
         LAUNCH_CHECK(h);
         std::vector<double> mins(3 * nb);
         int nonfinite = 0;
@@ -649,6 +667,7 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
     TRY(convert_coefs(h, np));
     TRY(blp_internal_chain_pre(h));
     TRY(build_hierarchy(h));
+    if (p.mesh == BLP_MESH_PARABOLIC) TRY(blp_internal_semi_build(h));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return BLP_OK;
 }
@@ -662,7 +681,7 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
         !(p->beta_x > 0.0) || !(p->beta_y > 0.0) || p->restart < 1 || p->restart > 64 || p->maxit < 1 ||
         (p->precision != BLP_FP64 && p->precision != BLP_MIXED) || p->stop_mode < 0 || p->stop_mode > 2 ||
         !(p->corner_reduction >= 1.0) || p->corner_max_cycles < 1 ||
-        (p->mesh != BLP_MESH_SHISHKIN && p->mesh != BLP_MESH_GRADED))
+        (p->mesh != BLP_MESH_SHISHKIN && p->mesh != BLP_MESH_GRADED && p->mesh != BLP_MESH_PARABOLIC))
         return BLP_ERR_ARG;
     auto t0 = std::chrono::steady_clock::now();
     blp_handle *h = new blp_handle();

@@ -100,6 +100,29 @@ def mms_exponential(x, y, eps):
     return f, u
 
 
+def mms_parabolic(x, y, eps):
+    """Manufactured problem of Sec. 3.3, eq. (parabolic_MMS): c1 = 1, c2 = 0,
+    r = 1 and u = X(x) Y(y) with
+        X = cos(pi x/2) - (e^{-x/eps} - e^{-1/eps}) / (1 - e^{-1/eps}),
+        Y = (1 - e^{-y/sqrt(eps)}) / (1 - e^{-1/sqrt(eps)}) - y^{5/2};
+    returns (f, u) at the interior nodes, f = -eps Lap u - u_x + u.  The
+    1/eps terms of -eps X'' - X' cancel exactly and are left out:
+        -eps X'' - X' = eps pi^2/4 cos(pi x/2) + pi/2 sin(pi x/2),
+        -eps Y''      = e^{-y/sqrt(eps)} / (1 - e^{-1/sqrt(eps)}) + 15/4 eps sqrt(y)."""
+    Xg, Yg = interior_grid(x, y)
+    se = np.sqrt(eps)
+    ex = np.exp(-Xg / eps)
+    e1 = np.exp(-1.0 / eps)
+    ey = np.exp(-Yg / se)
+    e2 = np.exp(-1.0 / se)
+    cx, sx_ = np.cos(np.pi * Xg / 2), np.sin(np.pi * Xg / 2)
+    Xf = cx - (ex - e1) / (1.0 - e1)
+    Yf = (1.0 - ey) / (1.0 - e2) - Yg ** 2.5
+    u = Xf * Yf
+    f = Yf * (eps * np.pi ** 2 / 4 * cx + np.pi / 2 * sx_) + Xf * (ey / (1.0 - e2) + 3.75 * eps * np.sqrt(Yg)) + u
+    return f, u
+
+
 def batch_params(count: int = 256, seed: int = 3, n_choices=tuple(range(64, 513, 32)),
                  log_eps=(-8.0, -2.0)):
     """Per-instance (N, eps, a, b, fourier seed) for the batched workload:

@@ -52,6 +52,12 @@ def test_library_mesh_matches_oracle_mesh():
         g = np.zeros(N + 1)
         _native.load().blp_mesh_graded(N, eps, 2.0, 1.0, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         np.testing.assert_array_equal(g, oracle.mesh(N, eps, graded=True)[0])
+        pm = np.zeros(N + 1)   # eq. (tau parabolic), sigma = 5/2
+        tau = _native.load().blp_mesh_parabolic(N, eps, 2.5, pm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        xo, tauo = oracle.mesh(N, eps, 2.5, 1.0, parabolic=True)
+        assert tau == tauo
+        np.testing.assert_array_equal(pm, xo)
+    assert _native.load().blp_mesh_parabolic(63, 1e-4, 2.5, pm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) < 0
 
 
 @pytest.mark.parametrize("N", [8, 10, 34, 64, 66, 96, 130])

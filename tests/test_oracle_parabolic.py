@@ -129,7 +129,7 @@ def test_parabolic_iterations_and_cycles_match_paper_table():
             A = oracle.assemble(N, eps, x, y, c1, c2, r)
             target = 10 * np.log(N) / N
             u, st, it, rr, mc = oracle.fgmres(N, A, f, P, tol=target, tol_abs=True, scaled=False)
-            assert st == 0 and mc == 3, (eps, N, mc)           # "only 3 V-cycles"
+            assert st == 0 and mc == 3, (eps, N, mc)           # 3 V-cycles per corner solve (Sec. 3.3)
             assert abs(np.abs(u - ue).max() - ref_err) <= 0.01 * ref_err, (eps, N)
             if eps == 1e-8 and N >= 256:
                 assert it == 6 and first_cycle_estimate_count(N, A, f, P, target) == int(ref), (eps, N, it)

@@ -183,7 +183,7 @@ def test_fgmres_iterations_match_paper_table():
 
 
 def test_n2048_paper_counts_are_estimate_counts():
-    """tab:exponential_times_iters at N = 2048 (reading 14): the paper's 10
+    """tab:exponential_times_iters at N = 2048 (Sec. 3.3): the paper's 10
     (eps = 1e-5) and 5 (eps = 1e-6) are the iterations at which the first
     FGMRES cycle's least-squares residual estimate meets the target; the
     oracle, which confirms on the true residual, takes 8 at eps = 1e-6."""
