@@ -67,6 +67,8 @@ typedef struct {
     int corner_fixed_cycles;   /* >0: exactly this many corner cycles (M becomes a fixed linear map) */
     int check_coefficients;    /* nonzero: blp_setup validates c1, c2, r (default 1) */
     int mesh;                  /* BLP_MESH_SHISHKIN (default), BLP_MESH_GRADED or BLP_MESH_PARABOLIC */
+    int layer_intervals;       /* NL: intervals on [0,tau] per axis, 0 (default) = N/2; other values
+                                  give the general Shishkin mesh of blp_mesh_q (BLP_MESH_SHISHKIN only) */
 } blp_params;
 
 #define BLP_MESH_SHISHKIN 0    /* piecewise-uniform layer mesh (blp_mesh) */
@@ -99,7 +101,8 @@ typedef struct {
 
 /* Fill *p with defaults: eps = 1e-4, N = 128, sigma = 2, beta = 1, restart
  * 30, maxit 20000, FP64, scaled stopping, corner_reduction 1e3, 50 max
- * cycles, no fixed cycles, coefficient checks on, Shishkin mesh. */
+ * cycles, no fixed cycles, coefficient checks on, Shishkin mesh with N/2
+ * layer intervals. */
 void blp_params_default(blp_params *p);
 
 /* S0. Shishkin mesh nodes (Sec. 2.2 eq. (tau 1D), Sec. 3 eq. (tau exponential)):
@@ -120,6 +123,17 @@ double blp_mesh(int N, double eps, double sigma, double beta, double *x);
  * (coarse nodes at even fine indices, transfer weights 1/2 and 1/4) are
  * unchanged on this mesh. */
 double blp_mesh_graded(int N, double eps, double sigma, double beta, double *x);
+
+/* General Shishkin mesh (the Remark on general Shishkin meshes): a share
+ * q = NL/N of the intervals in the layer, tau = min(q, sigma*eps*ln(N)/beta),
+ * NL equal intervals on [0,tau] and N-NL on [tau,1]:
+ *     x_i = (i/NL) tau for i <= NL,  x_i = tau + ((i-NL)/(N-NL)) (1-tau) above,
+ * x_N = 1.  NL = N/2 gives blp_mesh.  With blp_params.layer_intervals = NL the
+ * blocks of Sec. 3.1 split at layer index NL: C = nodes i, j <= NL, and so on
+ * (the paper develops the preconditioner for any number of layer and
+ * interior points).  1 <= NL <= N-2.  x: host array of N+1 doubles.
+ * Returns tau, or a negative value for invalid arguments. */
+double blp_mesh_q(int N, int NL, double eps, double sigma, double beta, double *x);
 
 /* Parabolic-layer mesh (Sec. 3, eq. (tau parabolic)), the y mesh of
  * BLP_MESH_PARABOLIC: tau = min(1/2, sigma sqrt(eps) ln(N)), N/2 equal
@@ -359,6 +373,12 @@ long long blp_kernel_launches(const blp_handle *h);
  * host overhead, so timed runs leave it off. */
 int blp_profile(blp_handle *h, int enable);
 int blp_profile_read(blp_handle *h, int cls, long long *count, double *total_ms, double *bytes);
+/* Dependency-chain length of the recorded launches of class cls: the sum,
+ * over its wavefront sweeps, of the steps a sweep cannot do in parallel
+ * (mx + my - 1 anti-diagonals of a downstream Gauss-Seidel sweep).  Times a
+ * step's latency it gives the latency floor the sweeps are measured against.
+ * 0 for classes that are not wavefronts. */
+int blp_profile_chain_steps(blp_handle *h, int cls, double *steps);
 int blp_kernel_class_count(void);
 const char *blp_kernel_class_name(int cls);
 

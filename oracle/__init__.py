@@ -50,6 +50,13 @@ def _load():
     lib.orc_band_solve.argtypes = [c_int, _D, _D, _D, _D, _D, _D, _D, c_int]
     lib.orc_prec_create.restype = c_void
     lib.orc_prec_create.argtypes = [c_int, c_double, _D, _D, _D, _D, _D, c_double, c_int, c_int, c_int, c_int, c_int]
+    lib.orc_prec_create_split.restype = c_void
+    lib.orc_prec_create_split.argtypes = [c_int, c_int, c_double, _D, _D, _D, _D, _D, c_double, c_int, c_int, c_int,
+                                          c_int, c_int]
+    lib.orc_prec_set_distance.restype = None
+    lib.orc_prec_set_distance.argtypes = [c_void, c_int]
+    lib.orc_mesh_q.restype = c_double
+    lib.orc_mesh_q.argtypes = [c_int, c_int, c_double, c_double, c_double, _D]
     lib.orc_semi_nlev.restype = c_int
     lib.orc_semi_nlev.argtypes = [c_void]
     lib.orc_semi_width.restype = c_int
@@ -99,13 +106,20 @@ def _f64(a) -> np.ndarray:
 COEFS = ("W", "E", "S", "N", "C")
 
 
-def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, parabolic: bool = False, graded: bool = False):
+def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, parabolic: bool = False, graded: bool = False,
+         layer_intervals: int | None = None):
     """Shishkin mesh nodes x[0..N] and the transition point tau (Sec. 2.2, Sec. 3).
 
     graded=True: the graded (Bakhvalov-Shishkin) layer mesh with the same tau
-    and N/2 split (the Remark after Theorem (big bound) covers graded meshes)."""
+    and N/2 split (the Remark after Theorem (big bound) covers graded meshes).
+    layer_intervals=NL: the general Shishkin mesh of the Remark on general
+    Shishkin meshes, NL = qN intervals on [0, tau], tau = min(q, ...)."""
     assert not (parabolic and graded)
     x = np.zeros(N + 1)
+    if layer_intervals is not None:
+        assert not (parabolic or graded)
+        tau = _load().orc_mesh_q(N, int(layer_intervals), eps, sigma, beta, _p(x))
+        return x, tau
     tau = _load().orc_mesh(N, eps, sigma, beta, 1 if parabolic else (2 if graded else 0), _p(x))
     return x, tau
 
@@ -151,19 +165,27 @@ class Prec:
     parabolic=True takes the corner cycle the paper gives for one parabolic
     and one exponential layer (x-semicoarsening, operator-induced
     interpolation, Galerkin coarse operators; forward application only); the
-    paper stops it at a 10^2 reduction (pass reduction=1e2)."""
+    paper stops it at a 10^2 reduction (pass reduction=1e2).
+    layer_intervals=NL splits the blocks at layer index NL instead of N/2
+    (the general Shishkin mesh of the Remark on general Shishkin meshes).
+    distance_transfer=True interpolates linearly in the level coordinates
+    (bilinear on a graded mesh) instead of with the index weights 1/2, 1/4."""
 
     def __init__(self, N, eps, x, y, c1, c2, r, reduction=1e3, max_cycles=50, fixed_cycles=0,
-                 coarsest_min=2, corner_exact=False, parabolic=False):
+                 coarsest_min=2, corner_exact=False, parabolic=False, layer_intervals=None,
+                 distance_transfer=False):
         self._lib = _load()
         self.N = N
         self.parabolic = parabolic
         self._keep = [_f64(a) for a in (x, y, c1, c2, r)]
-        h = self._lib.orc_prec_create(N, eps, *[_p(a) for a in self._keep], reduction, max_cycles,
-                                      fixed_cycles, coarsest_min, int(corner_exact), int(parabolic))
+        NL = N // 2 if layer_intervals is None else int(layer_intervals)
+        h = self._lib.orc_prec_create_split(N, NL, eps, *[_p(a) for a in self._keep], reduction, max_cycles,
+                                            fixed_cycles, coarsest_min, int(corner_exact), int(parabolic))
         if not h:
             raise ValueError("orc_prec_create rejected the arguments")
         self.h = ctypes.c_void_p(h)
+        if distance_transfer:
+            self._lib.orc_prec_set_distance(self.h, 1)
 
     def __del__(self):
         h = getattr(self, "h", None)

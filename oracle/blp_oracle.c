@@ -71,6 +71,26 @@ double orc_mesh(int N, double eps, double sigma, double beta, int kind, double *
 }
 
 /* ------------------------------------------------------------------------
+ * General Shishkin mesh (the Remark on general Shishkin meshes, Sec. 2.2):
+ * a share q = NL / N of the intervals in the layer, tau = min(q,
+ * sigma*eps*ln(N)/beta), NL equal intervals on [0,tau] and N - NL on
+ * [tau,1]: x_i = (i/NL)*tau for i <= NL, x_i = tau + ((i-NL)/(N-NL))*(1-tau)
+ * above, x_N = 1.  NL = N/2 is orc_mesh kind 0.  Returns tau.
+ * ---------------------------------------------------------------------- */
+double orc_mesh_q(int N, int NL, double eps, double sigma, double beta, double *x)
+{
+    double q = (double)NL / (double)N;
+    double tau = sigma * eps * log((double)N) / beta;
+    if (tau > q) tau = q;
+    for (int i = 0; i <= NL; i++) x[i] = ((double)i / (double)NL) * tau;
+    for (int i = NL + 1; i <= N; i++) x[i] = tau + ((double)(i - NL) / (double)(N - NL)) * (1.0 - tau);
+    x[0] = 0.0;
+    x[NL] = tau;
+    x[N] = 1.0;
+    return tau;
+}
+
+/* ------------------------------------------------------------------------
  * S1. Upwind 5-point stencil on a tensor grid (Sec. 3, the stencil display
  * after Fig. 4; 1D analogue eq. (stencil_1d)).  For an mx-by-my block of
  * nodes with coordinates xs[0..mx+1], ys[0..my+1] (index 0 and mx+1 / my+1
@@ -295,6 +315,7 @@ typedef struct {
     double reduction;
     int max_cycles, fixed_cycles, coarsest_min;
     int corner_exact;     /* 1: M_CC = A_CC solved by banded LU (the idealised M-hat) */
+    int distance;         /* 1: bilinear transfer weights from the level coordinates (graded meshes) */
     int last_cycles;
     double *wv;           /* work vectors */
     /* parabolic-layer corner cycle (semi != 0): x-semicoarsened levels of
@@ -328,14 +349,18 @@ void orc_prec_destroy(orc_prec *P)
 
 static void semi_build(orc_prec *P);
 
-orc_prec *orc_prec_create(int N, double eps, const double *x, const double *y,
-                          const double *c1, const double *c2, const double *r,
-                          double reduction, int max_cycles, int fixed_cycles, int coarsest_min,
-                          int corner_exact, int semi)
+/* The block split of Sec. 3.1 at layer index NL: layer set {1..NL} per axis
+ * (NL = N/2 on the mesh of Sec. 3; any NL for the general mesh of the
+ * Remark on general Shishkin meshes, whose analysis allows any number of
+ * layer and interior points). */
+orc_prec *orc_prec_create_split(int N, int NL, double eps, const double *x, const double *y,
+                                const double *c1, const double *c2, const double *r,
+                                double reduction, int max_cycles, int fixed_cycles, int coarsest_min,
+                                int corner_exact, int semi)
 {
-    if (N < 4 || (N & 1)) return NULL;
+    if (N < 4 || NL < 1 || NL > N - 2 || (semi && NL != N / 2)) return NULL;
     orc_prec *P = (orc_prec *)calloc(1, sizeof(orc_prec));
-    int M = N - 1, m = N / 2;
+    int M = N - 1, m = NL;
     size_t n = (size_t)M * M;
     P->N = N; P->m = m; P->eps = eps;
     P->reduction = reduction; P->max_cycles = max_cycles; P->fixed_cycles = fixed_cycles;
@@ -385,6 +410,21 @@ orc_prec *orc_prec_create(int N, double eps, const double *x, const double *y,
     if (semi) semi_build(P);
     return P;
 }
+
+orc_prec *orc_prec_create(int N, double eps, const double *x, const double *y,
+                          const double *c1, const double *c2, const double *r,
+                          double reduction, int max_cycles, int fixed_cycles, int coarsest_min,
+                          int corner_exact, int semi)
+{
+    if (N < 4 || (N & 1)) return NULL;
+    return orc_prec_create_split(N, N / 2, eps, x, y, c1, c2, r, reduction, max_cycles, fixed_cycles,
+                                 coarsest_min, corner_exact, semi);
+}
+
+/* Choose the transfer weights of the full-coarsening corner cycle: 0 the
+ * index weights of Sec. 3.2 (1/2, 1/4), 1 linear interpolation in the level
+ * coordinates (the same on the uniform corner of the mesh of Sec. 3). */
+void orc_prec_set_distance(orc_prec *P, int distance) { P->distance = distance; }
 
 int orc_prec_nlev(const orc_prec *P) { return P->nlev; }
 int orc_prec_level_size(const orc_prec *P, int l) { return P->ms[l]; }
@@ -437,43 +477,73 @@ void orc_mg_gs(orc_prec *P, int l, const double *b, double *e, int transpose)
 
 /* Bilinear interpolation from level l+1 (side mc) to level l (side mf):
  * ef += P ec.  Fine node (I,J) with I,J even coincides with coarse node
- * (I/2,J/2); odd indices average the two (or four) surrounding coarse nodes;
- * coarse index 0 is the Dirichlet boundary (value 0). */
+ * (I/2,J/2); odd indices take the two (or four) surrounding coarse nodes;
+ * coarse index 0 is the Dirichlet boundary (value 0).  The 1D weights of an
+ * odd fine index I are 1/2, 1/2 on the mesh of Sec. 3 (uniform in the
+ * corner), or, with P->distance, the distances to the two coarse nodes:
+ * (x_{I+1} - x_I) / (x_{I+1} - x_{I-1}) for coarse node (I-1)/2 and
+ * (x_I - x_{I-1}) / (x_{I+1} - x_{I-1}) for (I+1)/2 (the level-l coordinates),
+ * which is linear interpolation on a non-uniform (graded) mesh. */
 static double coarse_at(const double *ec, int mc, int I, int J)
 {
     if (I < 1 || J < 1 || I > mc || J > mc) return 0.0;
     return ec[(size_t)(J - 1) * mc + (I - 1)];
 }
+/* weights of the coarse nodes to the left and right of odd fine index I */
+static void lin_weights(const orc_prec *P, const double *c, int I, double *wl, double *wr)
+{
+    if (!P->distance) { *wl = 0.5; *wr = 0.5; return; }
+    double d = c[I + 1] - c[I - 1];
+    *wl = (c[I + 1] - c[I]) / d;
+    *wr = (c[I] - c[I - 1]) / d;
+}
 void orc_mg_prolong(orc_prec *P, int l, const double *ec, double *ef)
 {
     int mf = P->ms[l], mc = P->ms[l + 1];
+    const double *cx = P->lx[l], *cy = P->ly[l];
     for (int J = 1; J <= mf; J++)
         for (int I = 1; I <= mf; I++) {
-            double v;
+            double v, ax = 1.0, bx = 0.0, ay = 1.0, by = 0.0;
             int Ie = !(I & 1), Je = !(J & 1);
+            if (!Ie) lin_weights(P, cx, I, &ax, &bx);
+            if (!Je) lin_weights(P, cy, J, &ay, &by);
             if (Ie && Je) v = coarse_at(ec, mc, I / 2, J / 2);
-            else if (!Ie && Je) v = 0.5 * (coarse_at(ec, mc, (I - 1) / 2, J / 2) + coarse_at(ec, mc, (I + 1) / 2, J / 2));
-            else if (Ie && !Je) v = 0.5 * (coarse_at(ec, mc, I / 2, (J - 1) / 2) + coarse_at(ec, mc, I / 2, (J + 1) / 2));
-            else v = 0.25 * (coarse_at(ec, mc, (I - 1) / 2, (J - 1) / 2) + coarse_at(ec, mc, (I + 1) / 2, (J - 1) / 2)
-                             + coarse_at(ec, mc, (I - 1) / 2, (J + 1) / 2) + coarse_at(ec, mc, (I + 1) / 2, (J + 1) / 2));
+            else if (!Ie && Je) v = ax * coarse_at(ec, mc, (I - 1) / 2, J / 2) + bx * coarse_at(ec, mc, (I + 1) / 2, J / 2);
+            else if (Ie && !Je) v = ay * coarse_at(ec, mc, I / 2, (J - 1) / 2) + by * coarse_at(ec, mc, I / 2, (J + 1) / 2);
+            else if (!P->distance)
+                v = 0.25 * (coarse_at(ec, mc, (I - 1) / 2, (J - 1) / 2) + coarse_at(ec, mc, (I + 1) / 2, (J - 1) / 2)
+                            + coarse_at(ec, mc, (I - 1) / 2, (J + 1) / 2) + coarse_at(ec, mc, (I + 1) / 2, (J + 1) / 2));
+            else
+                v = ay * (ax * coarse_at(ec, mc, (I - 1) / 2, (J - 1) / 2) + bx * coarse_at(ec, mc, (I + 1) / 2, (J - 1) / 2))
+                    + by * (ax * coarse_at(ec, mc, (I - 1) / 2, (J + 1) / 2) + bx * coarse_at(ec, mc, (I + 1) / 2, (J + 1) / 2));
             ef[(size_t)(J - 1) * mf + (I - 1)] += v;
         }
 }
 
 /* bc = P^T rf (transpose of orc_mg_prolong), written as a plain scatter. */
-static void prolong_T(int mf, int mc, const double *rf, double *bc)
+static void prolong_T(const orc_prec *P, int l, const double *rf, double *bc)
 {
+    int mf = P->ms[l], mc = P->ms[l + 1];
+    const double *cx = P->lx[l], *cy = P->ly[l];
     for (size_t k = 0; k < (size_t)mc * mc; k++) bc[k] = 0.0;
     for (int J = 1; J <= mf; J++)
         for (int I = 1; I <= mf; I++) {
             double v = rf[(size_t)(J - 1) * mf + (I - 1)];
+            double ax = 1.0, bx = 0.0, ay = 1.0, by = 0.0;
             int Ie = !(I & 1), Je = !(J & 1);
+            if (!Ie) lin_weights(P, cx, I, &ax, &bx);
+            if (!Je) lin_weights(P, cy, J, &ay, &by);
 #define ADD(Ic, Jc, w) do { int _I = (Ic), _J = (Jc); if (_I >= 1 && _J >= 1 && _I <= mc && _J <= mc) bc[(size_t)(_J - 1) * mc + (_I - 1)] += (w) * v; } while (0)
             if (Ie && Je) ADD(I / 2, J / 2, 1.0);
-            else if (!Ie && Je) { ADD((I - 1) / 2, J / 2, 0.5); ADD((I + 1) / 2, J / 2, 0.5); }
-            else if (Ie && !Je) { ADD(I / 2, (J - 1) / 2, 0.5); ADD(I / 2, (J + 1) / 2, 0.5); }
-            else { ADD((I - 1) / 2, (J - 1) / 2, 0.25); ADD((I + 1) / 2, (J - 1) / 2, 0.25);
-                   ADD((I - 1) / 2, (J + 1) / 2, 0.25); ADD((I + 1) / 2, (J + 1) / 2, 0.25); }
+            else if (!Ie && Je) { ADD((I - 1) / 2, J / 2, ax); ADD((I + 1) / 2, J / 2, bx); }
+            else if (Ie && !Je) { ADD(I / 2, (J - 1) / 2, ay); ADD(I / 2, (J + 1) / 2, by); }
+            else if (!P->distance) {
+                ADD((I - 1) / 2, (J - 1) / 2, 0.25); ADD((I + 1) / 2, (J - 1) / 2, 0.25);
+                ADD((I - 1) / 2, (J + 1) / 2, 0.25); ADD((I + 1) / 2, (J + 1) / 2, 0.25);
+            } else {
+                ADD((I - 1) / 2, (J - 1) / 2, ax * ay); ADD((I + 1) / 2, (J - 1) / 2, bx * ay);
+                ADD((I - 1) / 2, (J + 1) / 2, ax * by); ADD((I + 1) / 2, (J + 1) / 2, bx * by);
+            }
 #undef ADD
         }
 }
@@ -487,11 +557,11 @@ void orc_mg_restrict(orc_prec *P, int l, const double *rf, double *bc, int trans
     if (!transpose) {
         double *t = dalloc(nf);
         for (size_t k = 0; k < nf; k++) t[k] = P->LD[l][k] * rf[k];
-        prolong_T(mf, mc, t, bc);
+        prolong_T(P, l, t, bc);
         for (size_t k = 0; k < nc; k++) bc[k] /= P->LD[l + 1][k];
         free(t);
     } else {
-        prolong_T(mf, mc, rf, bc);
+        prolong_T(P, l, rf, bc);
     }
 }
 

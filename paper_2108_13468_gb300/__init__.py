@@ -40,16 +40,20 @@ def default_params(**kw) -> Params:
     return p
 
 
-def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, graded: bool = False, parabolic: bool = False):
+def mesh(N: int, eps: float, sigma: float = 2.0, beta: float = 1.0, graded: bool = False, parabolic: bool = False,
+         layer_intervals: int | None = None):
     """Shishkin mesh nodes x[0..N] (blp_mesh) and the transition point tau;
     graded=True: the graded layer mesh with the same tau (blp_mesh_graded);
     parabolic=True: the parabolic-layer mesh, tau = min(1/2, sigma sqrt(eps)
-    ln N) (blp_mesh_parabolic; beta is not used)."""
-    if graded and parabolic:
-        raise ValueError("graded and parabolic are exclusive")
+    ln N) (blp_mesh_parabolic; beta is not used); layer_intervals=NL: the
+    general Shishkin mesh with NL intervals on [0, tau] (blp_mesh_q)."""
+    if graded + parabolic + (layer_intervals is not None) > 1:
+        raise ValueError("graded, parabolic and layer_intervals are exclusive")
     x = np.zeros(N + 1)
     xp = x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    if parabolic:
+    if layer_intervals is not None:
+        name, tau = "blp_mesh_q", N_.load().blp_mesh_q(N, int(layer_intervals), eps, sigma, beta, xp)
+    elif parabolic:
         name, tau = "blp_mesh_parabolic", N_.load().blp_mesh_parabolic(N, eps, sigma, xp)
     else:
         name = "blp_mesh_graded" if graded else "blp_mesh"

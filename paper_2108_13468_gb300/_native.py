@@ -26,7 +26,7 @@ class Params(ctypes.Structure):
     _fields_ = [("eps", c_double), ("N", c_int), ("sigma", c_double), ("beta_x", c_double), ("beta_y", c_double),
                 ("restart", c_int), ("maxit", c_int), ("precision", c_int), ("stop_mode", c_int),
                 ("corner_reduction", c_double), ("corner_max_cycles", c_int), ("corner_fixed_cycles", c_int),
-                ("check_coefficients", c_int), ("mesh", c_int)]
+                ("check_coefficients", c_int), ("mesh", c_int), ("layer_intervals", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -62,6 +62,7 @@ SIGNATURES = {
     "blp_mesh": (c_double, [c_int, c_double, c_double, c_double, _DP]),
     "blp_mesh_graded": (c_double, [c_int, c_double, c_double, c_double, _DP]),
     "blp_mesh_parabolic": (c_double, [c_int, c_double, c_double, _DP]),
+    "blp_mesh_q": (c_double, [c_int, c_int, c_double, c_double, c_double, _DP]),
     "blp_setup": (c_int, [ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]),
     "blp_set_stream": (c_int, [c_void_p, c_void_p]),
     "blp_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(Info)]),
@@ -74,6 +75,7 @@ SIGNATURES = {
     "blp_kernel_launches": (c_ll, [c_void_p]),
     "blp_profile": (c_int, [c_void_p, c_int]),
     "blp_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(c_ll), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "blp_profile_chain_steps": (c_int, [c_void_p, c_int, _DP]),
     "blp_kernel_class_count": (c_int, []),
     "blp_kernel_class_name": (ctypes.c_char_p, [c_int]),
     "blp_check_wait_timeout": (c_int, [c_void_p]),

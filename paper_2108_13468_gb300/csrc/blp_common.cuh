@@ -111,9 +111,11 @@ struct Layout {
     }
 };
 
-static inline Layout make_layout(int N) {
+// L: the last layer index (transition node) of the block split, N/2 unless
+// the general Shishkin mesh puts another number of intervals in the layer.
+static inline Layout make_layout(int N, int L = -1) {
     Layout Lt;
-    int L = N / 2;
+    if (L < 0) L = N / 2;
     Lt.N = N; Lt.L = L;
     long long off = 0;
     Lt.R[0] = make_region(LAYOUT_SKEW, L, L, 1, 1, off);            off += Lt.R[0].size;
@@ -237,6 +239,7 @@ struct ProfState {
     long long count[KC_COUNT] = {0};
     double ms[KC_COUNT] = {0.0};
     double bytes[KC_COUNT] = {0.0};   // algorithmic bytes of the recorded launches
+    double steps[KC_COUNT] = {0.0};   // wavefront steps on the dependency chain of the recorded launches
 };
 
 struct blp_handle {
@@ -314,9 +317,10 @@ int blp_internal_prof_flush(blp_handle *h);
 struct ProfScope {
     blp_handle *h;
     int slot = -1;
-    ProfScope(blp_handle *h_, int cls, double bytes = 0.0) : h(h_) {
+    ProfScope(blp_handle *h_, int cls, double bytes = 0.0, double steps = 0.0) : h(h_) {
         if (!h->prof.on) return;
         h->prof.bytes[cls] += bytes;
+        h->prof.steps[cls] += steps;
         if (h->prof.used * 2 + 2 > (int)h->prof.ev.size()) blp_internal_prof_flush(h);
         slot = h->prof.used++;
         h->prof.cls[slot] = cls;

@@ -546,8 +546,9 @@ static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls, bool la) {
     }
     const DtsShape sh = dts_shape<T, CH>(a.R.S, h->dts_max_cluster);
     if (DtsSmem<T, CH>::bytes(sh.WC, sh.NST) > 225 * 1024) return BLP_ERR_ARG;
-    // algorithmic words per node: beta, two couplings, out
-    ProfScope ps(h, cls, (double)a.R.mx * a.R.my * sizeof(T) * 4);
+    // algorithmic words per node: beta, two couplings, out; the chain has one
+    // step per anti-diagonal, mx + my - 1 of them
+    ProfScope ps(h, cls, (double)a.R.mx * a.R.my * sizeof(T) * 4, (double)(a.R.mx + a.R.my - 1));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -418,7 +418,8 @@ struct SemiCycler {
         constexpr int K = SweepK<T>::K;
         const int W = std::min(SEMI_WARPS, L.nb);
         const int P = sweep_spacing(K, L.S, W);
-        ProfScope ps(h, KC_DTS_GS, (double)n * 6 * sizeof(T));   // c0, 4 couplings read, e written
+        // c0, 4 couplings read, e written; the chain runs sx + 2 m - 2 steps
+        ProfScope ps(h, KC_DTS_GS, (double)n * 6 * sizeof(T), (double)(L.sx + 2 * L.m - 2));
         k_semi_gs<T, K><<<1, W * 32, 0, h->stream>>>(L, P, skip);
         LAUNCH_CHECK(h);
         return BLP_OK;

@@ -35,6 +35,22 @@ extern "C" double blp_mesh_graded(int N, double eps, double sigma, double beta, 
     return tau;
 }
 
+// General Shishkin mesh (the Remark on general Shishkin meshes): NL of the N
+// intervals on [0, tau], tau = min(NL/N, sigma eps ln N / beta).
+extern "C" double blp_mesh_q(int N, int NL, double eps, double sigma, double beta, double *x) {
+    if (N < 8 || NL < 1 || NL > N - 2 || !(eps > 0.0) || eps > 1.0 || !(beta > 0.0) || !(sigma > 0.0) || !x)
+        return -1.0;
+    const double q = (double)NL / (double)N;
+    double tau = sigma * eps * std::log((double)N) / beta;
+    if (tau > q) tau = q;
+    for (int i = 0; i <= NL; i++) x[i] = ((double)i / (double)NL) * tau;
+    for (int i = NL + 1; i <= N; i++) x[i] = tau + ((double)(i - NL) / (double)(N - NL)) * (1.0 - tau);
+    x[0] = 0.0;
+    x[NL] = tau;
+    x[N] = 1.0;
+    return tau;
+}
+
 // Parabolic-layer mesh in y (Sec. 3, eq. (tau parabolic)): tau = min(1/2,
 // sigma sqrt(eps) ln N), N/2 equal intervals on each side of tau.
 extern "C" double blp_mesh_parabolic(int N, double eps, double sigma, double *x) {
@@ -423,7 +439,7 @@ extern "C" int blp_profile(blp_handle *h, int enable) {
             P.cls.resize(4096);
             for (auto &e : P.ev) CUDA_TRY(cudaEventCreate(&e));
         }
-        for (int c = 0; c < KC_COUNT; c++) { P.count[c] = 0; P.ms[c] = 0.0; P.bytes[c] = 0.0; }
+        for (int c = 0; c < KC_COUNT; c++) { P.count[c] = 0; P.ms[c] = 0.0; P.bytes[c] = 0.0; P.steps[c] = 0.0; }
         P.used = 0;
         P.on = true;
     } else {
@@ -431,6 +447,12 @@ extern "C" int blp_profile(blp_handle *h, int enable) {
         P.on = false;
         return rc;
     }
+    return BLP_OK;
+}
+
+extern "C" int blp_profile_chain_steps(blp_handle *h, int cls, double *steps) {
+    if (!h || cls < 0 || cls >= KC_COUNT || !steps) return BLP_ERR_ARG;
+    *steps = h->prof.steps[cls];
     return BLP_OK;
 }
 
@@ -597,15 +619,20 @@ static int setup_impl(blp_handle *h, const double *c1, const double *c2, const d
     int N = p.N;
     long long n = (long long)(N - 1) * (N - 1);
     h->N = N;
-    h->L = N / 2;
-    h->lay = make_layout(N);
+    h->L = p.layer_intervals > 0 ? p.layer_intervals : N / 2;
+    h->lay = make_layout(N, h->L);
     long long np = h->lay.npad;
     h->hx.resize(N + 1);
     h->hy.resize(N + 1);
     auto mesh = p.mesh == BLP_MESH_GRADED ? blp_mesh_graded : blp_mesh;
-    h->tau_x = mesh(N, p.eps, p.sigma, p.beta_x, h->hx.data());
-    h->tau_y = p.mesh == BLP_MESH_PARABOLIC ? blp_mesh_parabolic(N, p.eps, p.sigma, h->hy.data())
-                                            : mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
+    if (h->L != N / 2) {   // general Shishkin mesh, NL = h->L intervals in the layer
+        h->tau_x = blp_mesh_q(N, h->L, p.eps, p.sigma, p.beta_x, h->hx.data());
+        h->tau_y = blp_mesh_q(N, h->L, p.eps, p.sigma, p.beta_y, h->hy.data());
+    } else {
+        h->tau_x = mesh(N, p.eps, p.sigma, p.beta_x, h->hx.data());
+        h->tau_y = p.mesh == BLP_MESH_PARABOLIC ? blp_mesh_parabolic(N, p.eps, p.sigma, h->hy.data())
+                                                : mesh(N, p.eps, p.sigma, p.beta_y, h->hy.data());
+    }
     TRY(dalloc(h, &h->x, N + 1));
     TRY(dalloc(h, &h->y, N + 1));
     CUDA_TRY(cudaMemcpyAsync(h->x, h->hx.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice, h->stream));
@@ -681,7 +708,9 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
         !(p->beta_x > 0.0) || !(p->beta_y > 0.0) || p->restart < 1 || p->restart > 64 || p->maxit < 1 ||
         (p->precision != BLP_FP64 && p->precision != BLP_MIXED) || p->stop_mode < 0 || p->stop_mode > 2 ||
         !(p->corner_reduction >= 1.0) || p->corner_max_cycles < 1 ||
-        (p->mesh != BLP_MESH_SHISHKIN && p->mesh != BLP_MESH_GRADED && p->mesh != BLP_MESH_PARABOLIC))
+        (p->mesh != BLP_MESH_SHISHKIN && p->mesh != BLP_MESH_GRADED && p->mesh != BLP_MESH_PARABOLIC) ||
+        p->layer_intervals < 0 || p->layer_intervals > p->N - 2 ||
+        (p->layer_intervals > 0 && p->layer_intervals != p->N / 2 && p->mesh != BLP_MESH_SHISHKIN))
         return BLP_ERR_ARG;
     auto t0 = std::chrono::steady_clock::now();
     blp_handle *h = new blp_handle();

@@ -109,7 +109,7 @@ int autotune(blp_handle *h, int reps, blp_tuning *best) {
     // (larger ones give the same launch); chunk lengths 8 / 16 / 32 (the
     // launch falls back to a shorter chunk where the stages do not fit);
     // the one- and two-step forms for this precision
-    const int strips = (h->N / 2 + 31) / 32;
+    const int strips = (std::max(h->L, h->N - 1 - h->L) + 31) / 32;
     std::vector<int> clusters;
     for (int c : {2, 4, 8, 16})
         if (c == 2 || c / 2 < strips) clusters.push_back(c);

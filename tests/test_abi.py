@@ -58,6 +58,14 @@ def test_library_mesh_matches_oracle_mesh():
         assert tau == tauo
         np.testing.assert_array_equal(pm, xo)
     assert _native.load().blp_mesh_parabolic(63, 1e-4, 2.5, pm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) < 0
+    for N, NL, eps in ((16, 4, 1e-3), (64, 48, 1e-6), (100, 30, 1e-2), (128, 64, 1e-8)):
+        qm = np.zeros(N + 1)
+        tau = _native.load().blp_mesh_q(N, NL, eps, 2.0, 1.0, qm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        xo, tauo = oracle.mesh(N, eps, layer_intervals=NL)
+        assert tau == tauo
+        np.testing.assert_array_equal(qm, xo)
+    qm = np.zeros(17)
+    assert _native.load().blp_mesh_q(16, 15, 1e-3, 2.0, 1.0, qm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) < 0
 
 
 @pytest.mark.parametrize("N", [8, 10, 34, 64, 66, 96, 130])

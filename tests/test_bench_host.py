@@ -19,14 +19,18 @@ def test_default_run_is_one_gpu_with_three_warmup_steps(monkeypatch):
 
 
 def test_roofline_object(monkeypatch):
-    monkeypatch.setattr(bench, "ncu_traffic", lambda cls: 1.5e6 if cls == "dts_gs" else None)
-    classes = {"dts_gs": {"GBps": 43.4, "share": 0.46}, "line_chain": {"GBps": 19.0, "share": 0.2}}
+    monkeypatch.setattr(bench, "ncu_traffic", lambda cls, pn: 1.5e6 if (cls, pn) == ("dts_gs", "fp64") else None)
+    by_prec = {"mixed": {"dts_gs": {"GBps": 43.4, "ms": 100.0, "launches": 10, "bytes": 4.34e9, "chain_steps": 2e5},
+                         "line_chain": {"GBps": 19.0, "ms": 50.0, "launches": 2, "bytes": 9.5e8}},
+               "fp64": {"dts_gs": {"GBps": 30.0, "ms": 300.0, "launches": 10, "bytes": 9e9, "chain_steps": 2e5}}}
     peak, _ = bench.measured_peak()
-    r = bench.roofline(classes)
-    assert r["kernel"] == "dts_gs" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["achieved"] == 43.4 and r["peak"] == peak and r["frac"] == round(43.4 / peak, 4)
-    assert r["traffic"] == 1.5e6 and r["share"] == 0.46
-    assert bench.roofline({}) is None
+    r = bench.roofline(by_prec, 2070.0)
+    assert (r["kernel"], r["precision"]) == ("dts_gs", "fp64") and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == 30.0 and r["peak"] == peak and r["frac"] == round(30.0 / peak, 4)
+    assert r["traffic"] == 1.5e6 and r["algorithmic_bytes_per_launch"] == 9e8
+    floor_ms = 2e5 * bench.CHAIN_STEP_CYCLES["fp64"] / 2070e3
+    assert r["chain_floor_ms"] == round(floor_ms, 3) and r["chain_floor_frac"] == round(floor_ms / 300.0, 4)
+    assert bench.roofline({}, 2070.0) is None
 
 
 def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
@@ -39,14 +43,16 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench.kernel_source_hash()
     rec = tmp_path / "profiles" / "roofline_traffic.md"
-    rec.write_text(f"source_hash: {h}\n\n| class | bytes per launch |\n|---|---|\n| dts_gs | 1289372 |\n")
-    assert bench.ncu_traffic("dts_gs") == 1289372.0
-    assert bench.ncu_traffic("line_chain") is None
+    rec.write_text(f"source_hash: {h}\n\n| class | precision | bytes per launch |\n|---|---|---|\n"
+                   "| dts_gs | fp64 | 1289372 |\n| dts_gs | mixed | 900000 |\n")
+    assert bench.ncu_traffic("dts_gs", "fp64") == 1289372.0
+    assert bench.ncu_traffic("dts_gs", "mixed") == 900000.0
+    assert bench.ncu_traffic("line_chain", "fp64") is None
     with open(dst / "blp_dts.cuh", "a") as fh:                # the kernel changed since the capture
         fh.write("\n// edited\n")
-    assert bench.kernel_source_hash() != h and bench.ncu_traffic("dts_gs") is None
+    assert bench.kernel_source_hash() != h and bench.ncu_traffic("dts_gs", "fp64") is None
     rec.unlink()
-    assert bench.ncu_traffic("dts_gs") is None
+    assert bench.ncu_traffic("dts_gs", "fp64") is None
 
 
 def test_committed_record_parses():

@@ -17,9 +17,10 @@ def _problem(N, eps, seed=0):
     return x, y, p, oracle.assemble(N, eps, x, y, p.c1, p.c2, p.r)
 
 
-def regions(N):
-    """Block label of each interior unknown (x-fastest): C, X, Y, I (Sec. 3.1)."""
-    m = N // 2
+def regions(N, NL=None):
+    """Block label of each interior unknown (x-fastest): C, X, Y, I (Sec. 3.1),
+    layer set {1..NL} per axis (NL = N/2 on the mesh of Sec. 3)."""
+    m = N // 2 if NL is None else NL
     lab = np.empty((N - 1, N - 1), "<U1")
     for j in range(1, N):
         for i in range(1, N):
@@ -27,14 +28,14 @@ def regions(N):
     return lab.ravel()
 
 
-def mhat_dense(N, A):
+def mhat_dense(N, A, NL=None):
     """The idealised M-hat of Sec. 3.1 built from the dense A by the
     definition eq. (2D blocks): block order C < X < Y < I, lower blocks
     zeroed, off-diagonal upper blocks exact, A_CC exact, and inside the
     diagonal blocks: M_II = upper-triangular part of A_II (E, N kept);
     M_YY drops W (keeps S, N, E); M_XX drops S (keeps W, E, N)."""
     D = oracle.dense(N, A)
-    lab = regions(N)
+    lab = regions(N, NL)
     order = {"C": 0, "X": 1, "Y": 2, "I": 3}
     n = D.shape[0]
     M = np.zeros_like(D)
@@ -69,6 +70,52 @@ def test_precond_definition_dense(N):
         np.testing.assert_allclose(z, np.linalg.solve(Mh, v), rtol=1e-9, atol=1e-12 * np.abs(z).max())
         zt, _ = P.apply(v, transpose=True)
         np.testing.assert_allclose(zt, np.linalg.solve(Mh.T, v), rtol=1e-9, atol=1e-12 * np.abs(zt).max())
+
+
+def test_general_shishkin_mesh_2d():
+    """The general Shishkin mesh (the Remark on general Shishkin meshes):
+    NL = qN equal intervals on [0, tau], N - NL on [tau, 1], tau = min(q,
+    sigma eps ln N / beta); q = 1/2 is the mesh of Sec. 3, node for node."""
+    for N, NL, eps in ((16, 4, 1e-3), (64, 48, 1e-6), (100, 30, 1e-2), (64, 16, 0.5)):
+        q = NL / N
+        x, tau = oracle.mesh(N, eps, layer_intervals=NL)
+        assert tau == min(q, 2.0 * eps * np.log(N)) and x[NL] == tau and x[0] == 0.0 and x[N] == 1.0
+        np.testing.assert_allclose(np.diff(x[:NL + 1]), tau / NL, rtol=1e-12)
+        np.testing.assert_allclose(np.diff(x[NL:]), (1 - tau) / (N - NL), rtol=1e-12)
+    for N, eps in ((64, 1e-4), (128, 1e-8)):
+        np.testing.assert_array_equal(oracle.mesh(N, eps, layer_intervals=N // 2)[0], oracle.mesh(N, eps)[0])
+
+
+@pytest.mark.parametrize("N,NL", [(16, 4), (16, 6), (16, 10), (16, 12), (14, 5)])
+def test_precond_definition_dense_general_split(N, NL):
+    """eq. (2D blocks) with the layer set {1..NL} of a general Shishkin mesh:
+    the oracle's block solves equal a dense solve with M-hat built from A by
+    the definition, forward and transposed."""
+    for eps in (1e-2, 1e-6):
+        x, _ = oracle.mesh(N, eps, layer_intervals=NL)
+        p = inputs.problem_fourier_quadratic(x, x, N, eps)
+        A = oracle.assemble(N, eps, x, x, p.c1, p.c2, p.r)
+        P = oracle.Prec(N, eps, x, x, p.c1, p.c2, p.r, corner_exact=True, layer_intervals=NL)
+        Mh = mhat_dense(N, A, NL)
+        v = np.random.default_rng(1).standard_normal((N - 1) ** 2)
+        z, _ = P.apply(v)
+        np.testing.assert_allclose(z, np.linalg.solve(Mh, v), rtol=1e-9, atol=1e-12 * np.abs(z).max())
+        zt, _ = P.apply(v, transpose=True)
+        np.testing.assert_allclose(zt, np.linalg.solve(Mh.T, v), rtol=1e-9, atol=1e-12 * np.abs(zt).max())
+
+
+@pytest.mark.parametrize("NL", [32, 96])
+def test_fgmres_general_split_reaches_direct_solution(NL):
+    """With the corner multigrid on the NL x NL corner, FGMRES reaches the
+    banded-LU solution of the general-mesh system."""
+    N, eps = 128, 1e-5
+    x, _ = oracle.mesh(N, eps, layer_intervals=NL)
+    p = inputs.problem_fourier_quadratic(x, x, N, eps)
+    A = oracle.assemble(N, eps, x, x, p.c1, p.c2, p.r)
+    P = oracle.Prec(N, eps, x, x, p.c1, p.c2, p.r, layer_intervals=NL)
+    u, st, it, rr, mc = oracle.fgmres(N, A, p.f, P, tol=1e-12)
+    ue = oracle.band_solve(N, A, p.f)
+    assert st == 0 and it < 60 and np.abs(u - ue).max() <= 1e-9 * np.abs(ue).max(), (it, mc)
 
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-5, 1e-8])
@@ -153,6 +200,36 @@ def test_interpolation_and_fe_restriction():
         lhs = (Lc["D"] * P.restrict(l, r)) @ ec
         rhs = (Lf["D"] * r) @ P.prolong(l, ec)
         assert np.isclose(lhs, rhs, rtol=1e-12)
+
+
+def test_distance_weighted_transfer_on_the_graded_mesh():
+    """Linear interpolation in the level coordinates (the option that makes
+    the transfer bilinear on a graded mesh): it reproduces x y on the graded
+    corner nodes, where the index weights 1/2, 1/4 do not, its restriction is
+    the FE-scaled adjoint, and on the mesh of Sec. 3 it equals the index
+    weights to rounding."""
+    N, eps = 64, 1e-6
+    x, _ = oracle.mesh(N, eps, graded=True)
+    p = inputs.problem_fourier_quadratic(x, x, N, eps)
+    Pd = oracle.Prec(N, eps, x, x, p.c1, p.c2, p.r, distance_transfer=True)
+    Pi = oracle.Prec(N, eps, x, x, p.c1, p.c2, p.r)
+    for l in range(Pd.nlev - 1):
+        xf, yf, Lf = Pd.level(l)
+        xc, yc, Lc = Pd.level(l + 1)
+        mf, mc = Pd.level_size(l), Pd.level_size(l + 1)
+        XC, YC = np.meshgrid(xc[1:mc + 1], yc[1:mc + 1])
+        XF, YF = np.meshgrid(xf[1:mf + 1], yf[1:mf + 1])
+        want = (XF * YF).ravel()
+        np.testing.assert_allclose(Pd.prolong(l, (XC * YC).ravel()), want, rtol=1e-12)
+        assert np.abs(Pi.prolong(l, (XC * YC).ravel()) - want).max() > 1e-3 * np.abs(want).max()
+        rng = np.random.default_rng(l)
+        r, ec = rng.standard_normal(mf * mf), rng.standard_normal(mc * mc)
+        assert np.isclose((Lc["D"] * Pd.restrict(l, r)) @ ec, (Lf["D"] * r) @ Pd.prolong(l, ec), rtol=1e-12)
+    xs, ys, ps, _ = _problem(N, eps)
+    Ps = oracle.Prec(N, eps, xs, ys, ps.c1, ps.c2, ps.r, distance_transfer=True)
+    Pu = oracle.Prec(N, eps, xs, ys, ps.c1, ps.c2, ps.r)
+    ec = np.random.default_rng(9).standard_normal(Ps.level_size(1) ** 2)
+    np.testing.assert_allclose(Ps.prolong(0, ec), Pu.prolong(0, ec), rtol=1e-13, atol=1e-13)
 
 
 def test_corner_cycle_count_matches_paper():
