@@ -268,7 +268,10 @@ def run_ours(args):
                       "N": N, "eps": eps_list, "precisions": [p for _, p in precisions], "tol": TOL,
                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write); working set > L2"},
            "gpu_launches": launches // args.steps, "clocks": clocks, "e2e": e2e, "roofline": roof,
-           "detail": detail, "kernel_classes": classes, "matched_sample": matched, "legs": legs}
+           "detail": detail, "kernel_classes": classes,
+           "kernel_classes_by_precision": {pn: {k: {kk: v[kk] for kk in ("launches", "ms", "share", "GBps")}
+                                                for k, v in cl.items()} for pn, cl in by_prec.items()},
+           "matched_sample": matched, "legs": legs}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(N)
         cpu = out["cpu_baseline"]["value"]

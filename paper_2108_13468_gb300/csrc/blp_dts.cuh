@@ -6,6 +6,7 @@
 #include "blp_common.cuh"
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
 
@@ -92,11 +93,21 @@ __device__ __forceinline__ void mbar_wait(unsigned long long *bar, unsigned pari
 
 // Shared-memory carve-up of one CTA: WC compute warps plus one copy warp.
 // Per compute warp: NST stages of CH diagonals of (cH, cV) pairs (T2) and
-// beta (T); an input ring of DTS_NSL slots of CH boundary values; full and
+// beta (T); an input ring of NSL slots of RS boundary values (DtsRing); full and
 // empty mbarriers per stage; one mbarrier per ring slot.  Then per compute
 // warp the count of ring slots its successor has released, the wave counter
 // and the abort flag.
-#define DTS_NSL 16
+// Hand-off granularity: boundary values per ring slot, and ring slots per
+// compute warp.  FP32 hands off whole chunks: its 34-cycle steps make the
+// per-slot wait, re-arm and stores cost more than a shorter lag between
+// strips saves (measured: 8-value slots made the 512^2 sweep 30% slower).
+// FP64 steps take ~220 cycles, and 8-value slots shorten the lag (measured
+// 3% faster).
+template <typename T, int CH>
+struct DtsRing {
+    static constexpr int RS = sizeof(T) == 4 ? CH : (CH < 8 ? CH : 8);
+    static constexpr int NSL = RS >= 16 ? 16 : 32;
+};
 
 template <typename T, int CH>
 struct DtsSmem {
@@ -104,9 +115,10 @@ struct DtsSmem {
     static constexpr size_t stage_pairs = (size_t)CH * 32 * sizeof(T2);
     static constexpr size_t stage_beta = (size_t)CH * 32 * sizeof(T);
     static constexpr size_t stage = stage_pairs + stage_beta;
-    static constexpr size_t ring = (size_t)DTS_NSL * CH * sizeof(T);
+    static constexpr int NSL = DtsRing<T, CH>::NSL;
+    static constexpr size_t ring = (size_t)NSL * DtsRing<T, CH>::RS * sizeof(T);
     static size_t bytes(int WC, int NST) {
-        return (size_t)WC * (NST * stage + ring + 16 * (size_t)NST + 8 * DTS_NSL + 4) + 64;
+        return (size_t)WC * (NST * stage + ring + 16 * (size_t)NST + 8 * (size_t)NSL + 4) + 64;
     }
 };
 
@@ -116,21 +128,20 @@ __device__ __forceinline__ unsigned mapa_u32(unsigned a, unsigned rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
     return r;
 }
-// CH boundary values into a (possibly peer) CTA's ring slot, as 16-byte
-// vector asynchronous stores whose bytes complete the transaction count of
-// that slot's mbarrier
-template <int CH>
-__device__ __forceinline__ void st_async_slot(unsigned addr, const float (&v)[CH], unsigned bar) {
+// RS boundary values (from a register array, compile-time offsets) into a
+// ring slot, as asynchronous vector stores completing the slot's mbarrier
+template <int RS>
+__device__ __forceinline__ void st_async_rs(unsigned addr, const float *v, unsigned bar) {
 #pragma unroll
-    for (int i = 0; i < CH / 4; i++)
+    for (int i = 0; i < RS / 4; i++)
         asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];\n"
                      ::"r"(addr + 16 * i), "r"(__float_as_uint(v[4 * i])), "r"(__float_as_uint(v[4 * i + 1])),
                      "r"(__float_as_uint(v[4 * i + 2])), "r"(__float_as_uint(v[4 * i + 3])), "r"(bar) : "memory");
 }
-template <int CH>
-__device__ __forceinline__ void st_async_slot(unsigned addr, const double (&v)[CH], unsigned bar) {
+template <int RS>
+__device__ __forceinline__ void st_async_rs(unsigned addr, const double *v, unsigned bar) {
 #pragma unroll
-    for (int i = 0; i < CH / 2; i++)
+    for (int i = 0; i < RS / 2; i++)
         asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];\n"
                      ::"r"(addr + 16 * i), "l"(__double_as_longlong(v[2 * i])), "l"(__double_as_longlong(v[2 * i + 1])),
                      "r"(bar) : "memory");
@@ -183,18 +194,21 @@ __device__ __forceinline__ void mbar_wait_cluster(unsigned long long *bar, unsig
         }
     }
 }
-// bounded wait until the local counter *ctr (written by a peer) >= target
-__device__ __forceinline__ void wait_counter(const unsigned *ctr, int target, volatile unsigned *abort_flag, int *err,
-                                             long long limit = BLP_SPIN_LIMIT) {
+// bounded wait until the local counter *ctr (written by a peer) >= target;
+// returns the last value read
+__device__ __forceinline__ int wait_counter(const unsigned *ctr, int target, volatile unsigned *abort_flag, int *err,
+                                            long long limit = BLP_SPIN_LIMIT) {
     long long n = 0;
-    while ((int)ld_acquire_cluster(ctr) < target) {
-        if (*abort_flag) return;
+    int v;
+    while ((v = (int)ld_acquire_cluster(ctr)) < target) {
+        if (*abort_flag) return v;
         if (++n > limit) {
             *abort_flag = 1u;
             atomicExch(err, BLP_ERR_TIMEOUT);
-            return;
+            return v;
         }
     }
+    return v;
 }
 
 // The kernel runs as one thread-block cluster of CL CTAs, each with WC
@@ -229,8 +243,13 @@ template <typename T, bool REV, int CH, bool BND, bool LA>
 __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
     static_assert(CH == 8 || CH == 16 || CH == 32, "ring slots carry 8, 16 or 32 values");
     static_assert(!(LA && BND), "the two-step form has no boundary-vector variant");
-    constexpr int SK = 31 / CH;   // the 31-row skew spans SK whole chunks
+    constexpr int DTS_RS = DtsRing<T, CH>::RS, DTS_NSL = DtsRing<T, CH>::NSL;
+    constexpr int NSUB = CH / DTS_RS;   // ring slots per chunk
+    constexpr int SKR = 31 / DTS_RS;    // the 31-row skew spans SKR whole slots
+    static_assert(CH % DTS_RS == 0 && DTS_RS % 4 == 0, "chunks hold whole ring slots");
     typedef typename Vec2T<T>::type T2;
+    typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
+    constexpr int VEC = 16 / sizeof(T);
     typedef DtsSmem<T, CH> SM;
     if (A.skip && *A.skip) return;   // same value in every CTA of the cluster
     cg::cluster_group cluster = cg::this_cluster();
@@ -252,6 +271,7 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
     const int qoff = REV ? D - (my + 31) : 0;   // padding diagonals come first in reversed order
     const int head = REV ? 0 : 31, tail = REV ? 31 : 0;
     const int nch = D / CH;
+    const int nsl = D / DTS_RS;   // ring slots per strip
 
     if (threadIdx.x < WC) relc[threadIdx.x] = 0u;
     if (threadIdx.x == 0) { *wave_done = 0u; *abort_flag = 0u; }
@@ -261,7 +281,7 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
             mbar_init(emptyb + w * NST + q, 1);
         }
         for (int q = 0; q < DTS_NSL; q++) mbar_init(rbars + w * DTS_NSL + q, 1);
-        for (int q = 0; q < DTS_NSL; q++) mbar_arrive_expect_tx(rbars + w * DTS_NSL + q, (unsigned)(CH * sizeof(T)));
+        for (int q = 0; q < DTS_NSL; q++) mbar_arrive_expect_tx(rbars + w * DTS_NSL + q, (unsigned)(DTS_RS * sizeof(T)));
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     cluster.sync();   // every CTA initialised before any peer writes into it
@@ -328,6 +348,7 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
 
     int k_in = 0, k_out = 0;   // strips consumed from g-1 / produced for g+1
     int seq = 0;               // chunks taken from the stages
+    int rel_seen = 0;          // successor's released-slot count as last read (it only grows)
 
     for (int k = 0;; k++) {
         const int sidx = g + k * W;
@@ -357,24 +378,6 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
                         hz[u] = __ldcg(A.out + R.off + (((long long)sprev * D + dprev) << 5) + (REV ? 31 : 0));
                 }
             }
-            if (has_in) {
-                const int upto = min(c + SK + 1, nch - 1);
-                for (; waited <= upto; waited++) {
-                    const int P = k_in * nch + waited;
-                    mbar_wait_cluster(myrbar + P % DTS_NSL, (unsigned)(P / DTS_NSL) & 1u, abort_flag, A.err);
-                }
-                // row t0+u-qoff left the producer at its step t0+u+31: slot
-                // c + (u+31)/CH, value (u+31) % CH, i.e. the last value of slot
-                // c+SK (u = 0) or value u-1 of slot c+SK+1 (u >= 1)
-                const int Pa = k_in * nch + c + SK, Pb = Pa + 1;
-                const T *sa = ring_w + (Pa % DTS_NSL) * CH, *sb = ring_w + (Pb % DTS_NSL) * CH;
-#pragma unroll
-                for (int u = 0; u < CH; u++) {
-                    const int row = t0 + u - qoff;
-                    const T v = u == 0 ? sa[CH - 1] : sb[u - 1];
-                    hz[u] = (row >= 0 && row < my) ? v : T(0);
-                }
-            }
             const int q = seq % NST;
             mbar_wait(myfull + q, (unsigned)(seq / NST) & 1u, abort_flag, A.err);
             const T2 *const pp = reinterpret_cast<const T2 *>(mystage + (size_t)q * SM::stage);
@@ -382,78 +385,110 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
             const bool is_head = lane == head;
             T *const op = outp + ((long long)(REV ? D - 1 - t0 : t0) << 5);
             T tz[CH];
-            if constexpr (LA) {
-                const bool next_head = lane == (REV ? 1 : 30);
-                const int nl = REV ? max(lane - 1, 0) : min(lane + 1, 31);   // upstream lane (clamped)
 #pragma unroll
-                for (int u = 0; u < CH; u += 2) {
-                    const int ui0 = REV ? CH - 1 - u : u, ui1 = REV ? CH - 2 - u : u + 1;
-                    const T2 c0 = pp[ui0 * 32 + lane], c1 = pp[ui1 * 32 + lane];
-                    const T b0 = pb[ui0 * 32 + lane], b1 = pb[ui1 * 32 + lane];
-                    T2 n0 = pp[ui0 * 32 + nl];
-                    T nb0 = pb[ui0 * 32 + nl];
-                    if (is_head) { n0.x = T(0); n0.y = T(0); nb0 = hz[u + 1]; }
-                    const T K = b1 - c1.y * b0 - c1.x * nb0;
-                    const T Ac = c1.y * c0.y, Bc = c1.y * c0.x + c1.x * n0.y, Cc = c1.x * n0.x;
-                    T Z1 = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
-                    T Z2 = REV ? __shfl_up_sync(FULL, zprev, 2) : __shfl_down_sync(FULL, zprev, 2);
-                    Z1 = is_head ? hz[u] : Z1;
-                    Z2 = is_head ? T(0) : (next_head ? hz[u] : Z2);
-                    T z1 = K + Ac * zprev;
-                    z1 = z1 + Bc * Z1;
-                    z1 = z1 + Cc * Z2;
-                    T z0 = b0 - c0.y * zprev;
-                    z0 = z0 - c0.x * Z1;
-                    op[REV ? -(u << 5) : (u << 5)] = z0;
-                    op[REV ? -((u + 1) << 5) : ((u + 1) << 5)] = z1;
-                    tz[u] = z0;
-                    tz[u + 1] = z1;
-                    zprev = z1;
-                }
-            } else {
+            for (int i = 0; i < NSUB; i++) {
+                const int n = c * NSUB + i;   // sub-chunk of this strip: steps t0 + i*RS .. +RS-1
+                if (has_in) {
+                    const int upto = min(n + SKR + 1, nsl - 1);
+                    for (; waited <= upto; waited++) {
+                        const int P = k_in * nsl + waited;
+                        mbar_wait_cluster(myrbar + P % DTS_NSL, (unsigned)(P / DTS_NSL) & 1u, abort_flag, A.err);
+                    }
+                    // row t0+u-qoff left the producer at its step t0+u+31: slot
+                    // (t0+u+31)/RS, value (t0+u+31) % RS, i.e. for u = i*RS + j the
+                    // last value of slot n+SKR (j = 0) or value j-1 of slot n+SKR+1
+                    const int Pa = k_in * nsl + n + SKR, Pb = Pa + 1;
+                    const T *sa = ring_w + (Pa % DTS_NSL) * DTS_RS, *sb = ring_w + (Pb % DTS_NSL) * DTS_RS;
+                    T sbv[DTS_RS];
 #pragma unroll
-            for (int u = 0; u < CH; u++) {
-                const int ui = REV ? CH - 1 - u : u;
-                const T2 cpair = pp[ui * 32 + lane];
-                const T beta = pb[ui * 32 + lane];
-                T zH = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
-                zH = is_head ? hz[u] : zH;
-                T zV = zprev;
-                if (BND) {   // reversed interior sweep: west / south neighbours in the X / Y blocks
-                    const int ktop = (REV ? D - 1 - (t0 + u) : t0 + u) - 31 + lane;
-                    const int a = s * 32 + lane, b = my - 1 - ktop;
-                    if (ktop >= 0 && ktop < my && a < R.mx) {
-                        if (a == 0) zH = A.bnd[A.lay.addr(R.i0 - 1, R.j0 + b)];
-                        if (b == 0) zV = A.bnd[A.lay.addr(R.i0 + a, R.j0 - 1)];
+                    for (int e = 0; e < DTS_RS; e += VEC)   // slots are 16-byte aligned: vector reads
+                        *reinterpret_cast<V *>(sbv + e) = *reinterpret_cast<const V *>(sb + e);
+#pragma unroll
+                    for (int j = 0; j < DTS_RS; j++) {
+                        const int row = t0 + i * DTS_RS + j - qoff;
+                        const T v = j == 0 ? sa[DTS_RS - 1] : sbv[j - 1];
+                        hz[i * DTS_RS + j] = (row >= 0 && row < my) ? v : T(0);
                     }
                 }
-                T z = beta - cpair.y * zV;
-                z = z - cpair.x * zH;
-                op[REV ? -(u << 5) : (u << 5)] = z;
-                tz[u] = z;
-                zprev = z;
+                if constexpr (LA) {
+                    const bool next_head = lane == (REV ? 1 : 30);
+                    const int nl = REV ? max(lane - 1, 0) : min(lane + 1, 31);   // upstream lane (clamped)
+#pragma unroll
+                    for (int u = i * DTS_RS; u < i * DTS_RS + DTS_RS; u += 2) {
+                        const int ui0 = REV ? CH - 1 - u : u, ui1 = REV ? CH - 2 - u : u + 1;
+                        const T2 c0 = pp[ui0 * 32 + lane], c1 = pp[ui1 * 32 + lane];
+                        const T b0 = pb[ui0 * 32 + lane], b1 = pb[ui1 * 32 + lane];
+                        T2 n0 = pp[ui0 * 32 + nl];
+                        T nb0 = pb[ui0 * 32 + nl];
+                        if (is_head) { n0.x = T(0); n0.y = T(0); nb0 = hz[u + 1]; }
+                        const T K = b1 - c1.y * b0 - c1.x * nb0;
+                        const T Ac = c1.y * c0.y, Bc = c1.y * c0.x + c1.x * n0.y, Cc = c1.x * n0.x;
+                        T Z1 = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
+                        T Z2 = REV ? __shfl_up_sync(FULL, zprev, 2) : __shfl_down_sync(FULL, zprev, 2);
+                        Z1 = is_head ? hz[u] : Z1;
+                        Z2 = is_head ? T(0) : (next_head ? hz[u] : Z2);
+                        T z1 = K + Ac * zprev;
+                        z1 = z1 + Bc * Z1;
+                        z1 = z1 + Cc * Z2;
+                        T z0 = b0 - c0.y * zprev;
+                        z0 = z0 - c0.x * Z1;
+                        op[REV ? -(u << 5) : (u << 5)] = z0;
+                        op[REV ? -((u + 1) << 5) : ((u + 1) << 5)] = z1;
+                        tz[u] = z0;
+                        tz[u + 1] = z1;
+                        zprev = z1;
+                    }
+                } else {
+#pragma unroll
+                    for (int u = i * DTS_RS; u < i * DTS_RS + DTS_RS; u++) {
+                        const int ui = REV ? CH - 1 - u : u;
+                        const T2 cpair = pp[ui * 32 + lane];
+                        const T beta = pb[ui * 32 + lane];
+                        T zH = REV ? __shfl_up_sync(FULL, zprev, 1) : __shfl_down_sync(FULL, zprev, 1);
+                        zH = is_head ? hz[u] : zH;
+                        T zV = zprev;
+                        if (BND) {   // reversed interior sweep: west / south neighbours in the X / Y blocks
+                            const int ktop = (REV ? D - 1 - (t0 + u) : t0 + u) - 31 + lane;
+                            const int a = s * 32 + lane, b = my - 1 - ktop;
+                            if (ktop >= 0 && ktop < my && a < R.mx) {
+                                if (a == 0) zH = A.bnd[A.lay.addr(R.i0 - 1, R.j0 + b)];
+                                if (b == 0) zV = A.bnd[A.lay.addr(R.i0 + a, R.j0 - 1)];
+                            }
+                        }
+                        T z = beta - cpair.y * zV;
+                        z = z - cpair.x * zH;
+                        op[REV ? -(u << 5) : (u << 5)] = z;
+                        tz[u] = z;
+                        zprev = z;
+                    }
+                }
+                if (has_out) {
+                    const int P = k_out * nsl + n;   // slot sequence number in the successor's ring
+                    // the slot is free once the successor has released P - DTS_NSL + 1 slots;
+                    // read its counter only when the last value seen does not show that
+                    if (P - DTS_NSL + 1 > rel_seen) rel_seen = wait_counter(relc + w, P - DTS_NSL + 1, abort_flag, A.err);
+                    if (lane == tail)
+                        st_async_rs<DTS_RS>(succ_ring + (unsigned)((P % DTS_NSL) * DTS_RS * sizeof(T)), tz + i * DTS_RS,
+                                    succ_rbar + (unsigned)((P % DTS_NSL) * 8));
+                }
+                __syncwarp();   // every lane has read this sub-chunk's ring slots
+                if (has_in && lane == head && !*abort_flag) {
+                    // slots no later sub-chunk reads: re-arm for their next use, release
+                    const int rel = n == nsl - 1 ? nsl : min(n + SKR + 1, nsl);
+                    for (; released < rel; released++) {
+                        const int P = k_in * nsl + released;
+                        mbar_arrive_expect_tx(myrbar + P % DTS_NSL, (unsigned)(DTS_RS * sizeof(T)));
+                    }
+                    // the count reaches the predecessor every fourth sub-chunk and at
+                    // the strip's end: it trails the true count by at most three
+                    // slots, while the producer needs it only DTS_NSL - 1 slots
+                    // ahead of the slots this warp still waits for (n + SKR + 1)
+                    if ((n & 3) == 3 || n == nsl - 1) st_relaxed_cluster(pred_rel, (unsigned)(k_in * nsl + released));
+                }
+                __syncwarp();
             }
-            }
-            __syncwarp();
             if (lane == 0) mbar_arrive(myempty + q);   // stage read: the copy warp may refill it
             seq++;
-            if (has_out) {
-                const int P = k_out * nch + c;   // slot sequence number in the successor's ring
-                wait_counter(relc + w, P - DTS_NSL + 1, abort_flag, A.err);
-                if (lane == tail)
-                    st_async_slot<CH>(succ_ring + (unsigned)((P % DTS_NSL) * CH * sizeof(T)), tz,
-                                  succ_rbar + (unsigned)((P % DTS_NSL) * 8));
-            }
-            if (has_in && lane == head && !*abort_flag) {
-                // slots no later chunk reads: re-arm for their next use, release
-                const int rel = c == nch - 1 ? nch : min(c + SK + 1, nch);
-                for (; released < rel; released++) {
-                    const int P = k_in * nch + released;
-                    mbar_arrive_expect_tx(myrbar + P % DTS_NSL, (unsigned)(CH * sizeof(T)));
-                }
-                st_relaxed_cluster(pred_rel, (unsigned)(k_in * nch + released));
-            }
-            __syncwarp();
         }
         if (has_in) k_in++;
         if (has_out) k_out++;
