@@ -319,7 +319,9 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
                     }
                     any = true;
                 }
-                if (!any && ++n > BLP_SPIN_LIMIT) {   // compute warps stopped consuming
+                if (any) {
+                    n = 0;   // counts consecutive idle polls only
+                } else if (++n > BLP_SPIN_LIMIT) {   // compute warps stopped consuming
                     *abort_flag = 1u;
                     atomicExch(A.err, BLP_ERR_TIMEOUT);
                     break;

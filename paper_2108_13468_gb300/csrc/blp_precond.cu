@@ -734,6 +734,7 @@ struct CoarseArgs {
     double red2;                      // reduction factor squared
     DevState *st;
     const int *skip;
+    int *err;                         // bounded-wait failures (BLP_ERR_TIMEOUT)
 };
 
 // Shared-memory image of one level inside the fused kernel (natural layout):
@@ -745,6 +746,7 @@ template <typename T>
 struct CLev {
     int m;
     T *e, *b, *cw, *ce, *cs, *cn, *om, *wt;
+    T *c0;   // scratch of the sweep's right-hand side (shared by all levels)
 };
 
 // r = b - Op e at node (a, b) of a level (Op: normalised operator, or its transpose)
@@ -782,11 +784,130 @@ __device__ __forceinline__ void coarse_gs_body(const CLev<T> L, int a, bool warp
     }
 }
 
+// The same sweep for levels up to 64 wide, without a barrier per diagonal.
+// A CTA-parallel pass first forms c0 = b - (terms of the neighbours the sweep
+// reaches later, still old: W and S forward, E and N transposed).  One warp
+// then runs the wavefront with the new neighbour values in registers: the
+// node's own column's last value (N forward, S transposed) and, through one
+// shuffle, the adjacent lane's (E forward, W transposed).  Lane l owns column
+// l (m <= 32) or columns 2l, 2l+1 (m <= 64); with two columns the second
+// column's chain neighbour is the lane's own first column.  The node of
+// column a handled at step t lies on row b = (2m-2-t) - a forward, t - a
+// transposed; outside the level a lane carries 0.
+template <typename T, bool TRANS>
+__device__ __forceinline__ void coarse_gs_chain(const CLev<T> L) {
+    const int m = L.m, n = m * m;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int a = k % m, bb = k / m;
+        T s = L.b[k];
+        if (!TRANS) {
+            if (a > 0) s -= L.cw[k] * L.e[k - 1];
+            if (bb > 0) s -= L.cs[k] * L.e[k - m];
+        } else {
+            if (a < m - 1) s -= L.ce[k] * L.e[k + 1];
+            if (bb < m - 1) s -= L.cn[k] * L.e[k + m];
+        }
+        L.c0[k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        // chain couplings: forward E (horizontal) and N (vertical), transposed W and S
+        const T *__restrict__ ch = TRANS ? L.cw : L.ce;
+        const T *__restrict__ cv = TRANS ? L.cs : L.cn;
+        const T *__restrict__ c0 = L.c0;
+        T *__restrict__ e = L.e;
+        const int nst = 2 * m - 1;
+        const int dk = TRANS ? m : -m;   // node index change per step along a column
+        // column a is on the level during steps [lo(a), lo(a) + m - 1]: forward
+        // from row m-1 at step m-1-a down to row 0, transposed from row 0 at step a
+        auto first_step = [&](int a) { return TRANS ? a : m - 1 - a; };
+        auto first_node = [&](int a) { return TRANS ? a : (m - 1) * m + a; };
+        constexpr int G = 4;   // steps per group: their shared-memory loads are issued together
+        if (m <= 32) {
+            T z = T(0);
+            const int a = lane;
+            const bool live = a < m, headl = lane == (TRANS ? 0 : 31);
+            const int lo = first_step(a);
+            int k = first_node(a) - lo * dk;   // the (virtual) node index at step 0
+            for (int t0 = 0; t0 < nst; t0 += G, k += G * dk) {
+                T cc[G], cvv[G], chh[G];
+                bool ok[G];
+#pragma unroll
+                for (int u = 0; u < G; u++) {
+                    ok[u] = live && (unsigned)(t0 + u - lo) < (unsigned)m;
+                    const int ku = k + u * dk;
+                    cc[u] = ok[u] ? c0[ku] : T(0);
+                    cvv[u] = ok[u] ? cv[ku] : T(0);
+                    chh[u] = ok[u] && !headl ? ch[ku] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < G; u++) {
+                    const T zh = TRANS ? __shfl_up_sync(FULL, z, 1) : __shfl_down_sync(FULL, z, 1);
+                    T v = cc[u] - cvv[u] * z;
+                    v = v - chh[u] * zh;
+                    if (ok[u]) e[k + u * dk] = v;
+                    z = ok[u] ? v : T(0);
+                }
+            }
+        } else {
+            // columns a0 = 2 lane, a1 = 2 lane + 1; z0, z1 their last values
+            T z0 = T(0), z1 = T(0);
+            const int a0 = 2 * lane, a1 = a0 + 1;
+            const bool live0 = a0 < m, live1 = a1 < m, headl = lane == (TRANS ? 0 : 31);
+            const int lo0 = first_step(a0), lo1 = first_step(a1);
+            int k0 = first_node(a0) - lo0 * dk, k1 = first_node(a1) - lo1 * dk;
+            for (int t0 = 0; t0 < nst; t0 += G, k0 += G * dk, k1 += G * dk) {
+                T c0a[G], cva[G], cha[G], c0b[G], cvb[G], chb[G];
+                bool oka[G], okb[G];
+#pragma unroll
+                for (int u = 0; u < G; u++) {
+                    oka[u] = live0 && (unsigned)(t0 + u - lo0) < (unsigned)m;
+                    okb[u] = live1 && (unsigned)(t0 + u - lo1) < (unsigned)m;
+                    const int ka = k0 + u * dk, kb = k1 + u * dk;
+                    c0a[u] = oka[u] ? c0[ka] : T(0);
+                    cva[u] = oka[u] ? cv[ka] : T(0);
+                    cha[u] = oka[u] && !(TRANS && headl) ? ch[ka] : T(0);
+                    c0b[u] = okb[u] ? c0[kb] : T(0);
+                    cvb[u] = okb[u] ? cv[kb] : T(0);
+                    chb[u] = okb[u] && !(!TRANS && headl) ? ch[kb] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < G; u++) {
+                    // forward: E of column a1 is the next lane's column a0; transposed: W of
+                    // column a0 is the previous lane's column a1
+                    const T zh = TRANS ? __shfl_up_sync(FULL, z1, 1) : __shfl_down_sync(FULL, z0, 1);
+                    T v0, v1;
+                    if (!TRANS) {
+                        // (a1, b1): E = next lane's column a0, N = own z1
+                        v1 = c0b[u] - cvb[u] * z1;
+                        v1 = v1 - chb[u] * zh;
+                        // (a0, b0 = b1 + 1): E = (a1, b1 + 1) = own z1 (last step), N = own z0
+                        v0 = c0a[u] - cva[u] * z0;
+                        v0 = v0 - cha[u] * z1;
+                    } else {
+                        // (a0, b0): W = previous lane's column a1, S = own z0
+                        v0 = c0a[u] - cva[u] * z0;
+                        v0 = v0 - cha[u] * zh;
+                        // (a1, b1 = b0 - 1): W = (a0, b0 - 1) = own z0 (last step), S = own z1
+                        v1 = c0b[u] - cvb[u] * z1;
+                        v1 = v1 - chb[u] * z0;
+                    }
+                    if (oka[u]) e[k0 + u * dk] = v0;
+                    if (okb[u]) e[k1 + u * dk] = v1;
+                    z0 = oka[u] ? v0 : T(0);
+                    z1 = okb[u] ? v1 : T(0);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, bool TRANS>
 __device__ __forceinline__ void coarse_gs(const CLev<T> L) {
-    if (L.m <= 32) {
-        if (threadIdx.x < 32) coarse_gs_body<T, TRANS>(L, threadIdx.x, true);
-        __syncthreads();
+    if (L.m <= 64) {
+        coarse_gs_chain<T, TRANS>(L);
     } else {
         coarse_gs_body<T, TRANS>(L, threadIdx.x, false);   // m <= blockDim.x
     }
@@ -815,9 +936,36 @@ __global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
             L.wt = TRANS ? p : L.om;
             if (TRANS) p += n;
         }
+        for (int l = A.l0; l < A.nlev; l++) LV[l].c0 = p;   // sweep scratch, the size of level l0
+    }
+    // the static coefficients: one 1D bulk copy per array when every array
+    // is a whole number of 16-byte units (then all offsets are aligned too),
+    // else element by element below
+    __shared__ __align__(8) unsigned long long cbar;
+    bool bulk = true;
+    for (int l = A.l0; l < A.nlev; l++) bulk = bulk && (A.m[l] * A.m[l] * (int)sizeof(T)) % 16 == 0;
+    if (bulk && threadIdx.x == 0) {
+        unsigned bytes = 0;
+        for (int l = A.l0; l < A.nlev; l++) bytes += (TRANS ? 6u : 5u) * (unsigned)(A.m[l] * A.m[l] * sizeof(T));
+        mbar_init(&cbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_arrive_expect_tx(&cbar, bytes);
+        for (int l = A.l0; l < A.nlev; l++) {
+            const int n = A.m[l] * A.m[l];
+            const unsigned nb = (unsigned)(n * sizeof(T));
+            const CLev<T> &L = LV[l];
+            const T *nat = A.nat[l];
+            const int q0 = TRANS ? 4 : 0;
+            bulk_g2s(L.cw, nat + (long long)(q0 + 0) * n, nb, &cbar);
+            bulk_g2s(L.ce, nat + (long long)(q0 + 1) * n, nb, &cbar);
+            bulk_g2s(L.cs, nat + (long long)(q0 + 2) * n, nb, &cbar);
+            bulk_g2s(L.cn, nat + (long long)(q0 + 3) * n, nb, &cbar);
+            bulk_g2s(L.om, nat + (long long)8 * n, nb, &cbar);
+            if (TRANS) bulk_g2s(L.wt, nat + (long long)9 * n, nb, &cbar);
+        }
     }
     __syncthreads();
-    {
+    if (!bulk) {
         for (int l = A.l0; l < A.nlev; l++) {
             const int n = A.m[l] * A.m[l];
             const CLev<T> L = LV[l];
@@ -865,6 +1013,15 @@ __global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
             if (k < m0 * m0) { LV[l0].b[k] = v[u]; LV[l0].e[k] = T(0); }
         }
     }
+    if (bulk) {   // the copies read valid memory and complete; the wait is bounded all the same
+        long long it = 0;
+        while (!mbar_try_wait(&cbar, 0u)) {
+            if (++it > (BLP_SPIN_LIMIT >> 4)) {
+                if (threadIdx.x == 0) atomicExch(A.err, BLP_ERR_TIMEOUT);
+                break;
+            }
+        }
+    }
     __syncthreads();
 
     auto vcycle = [&]() {
@@ -872,7 +1029,14 @@ __global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
             const CLev<T> F = LV[l], Cc = LV[l + 1];
             const int m = F.m, mc = Cc.m;
             coarse_gs<T, TRANS>(F);
-            // restriction of the residual: forward b_c = omega_c^-1 P^T omega_f r, transpose b_c = P^T r
+            // restriction of the residual: forward b_c = omega_c^-1 P^T omega_f r, transpose
+            // b_c = P^T r; the (scaled) residual of every fine node once, into the scratch
+            for (int k = threadIdx.x; k < m * m; k += blockDim.x) {
+                T r = coarse_residual<T>(F, k % m, k / m);
+                if (!TRANS) r *= F.om[k];
+                F.c0[k] = r;
+            }
+            __syncthreads();
             for (int q = threadIdx.x; q < mc * mc; q += blockDim.x) {
                 const int a0 = 2 * (q % mc) + 1, b0 = 2 * (q / mc) + 1;
                 T sum = T(0);
@@ -882,9 +1046,7 @@ __global__ void __launch_bounds__(256) k_mg_coarse(CoarseArgs<T> A) {
                     for (int da = -1; da <= 1; da++) {
                         const int a = a0 + da;
                         if (a < 0 || a >= m) continue;
-                        T r = coarse_residual<T>(F, a, bb);
-                        if (!TRANS) r *= F.om[bb * m + a];
-                        sum += (da == 0 ? T(1) : T(0.5)) * (db == 0 ? T(1) : T(0.5)) * r;
+                        sum += (da == 0 ? T(1) : T(0.5)) * (db == 0 ? T(1) : T(0.5)) * F.c0[bb * m + a];
                     }
                 }
                 Cc.b[q] = TRANS ? sum : sum / Cc.om[q];
@@ -965,7 +1127,7 @@ template <typename T>
 static size_t coarse_smem(const Hierarchy<T> &H, int l0) {
     size_t b = 0;
     for (int l = l0; l < H.nlev; l++) b += 8 * sizeof(T) * (size_t)H.lev[l].R.mx * H.lev[l].R.mx;
-    return b;
+    return b + sizeof(T) * (size_t)H.lev[l0].R.mx * H.lev[l0].R.mx;   // + the sweep scratch
 }
 
 // first level handled by the fused coarse kernel (-1: none)
@@ -985,7 +1147,7 @@ static int launch_coarse(blp_handle *h, Hierarchy<T> &H, int l0, const T *b_in, 
     a.b_in = b_in; a.e_out = e_out; a.R0 = H.lev[l0].R;
     a.full = full; a.fixed_cycles = h->p.corner_fixed_cycles; a.max_cycles = h->p.corner_max_cycles;
     a.red2 = h->p.corner_reduction * h->p.corner_reduction;
-    a.st = h->dev; a.skip = skip;
+    a.st = h->dev; a.skip = skip; a.err = h->err;
     const size_t smem = coarse_smem(H, l0);
     static std::atomic<bool> attr{false};
     if (!attr) {
