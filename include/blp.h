@@ -69,6 +69,15 @@ typedef struct {
     int mesh;                  /* BLP_MESH_SHISHKIN (default), BLP_MESH_GRADED or BLP_MESH_PARABOLIC */
     int layer_intervals;       /* NL: intervals on [0,tau] per axis, 0 (default) = N/2; other values
                                   give the general Shishkin mesh of blp_mesh_q (BLP_MESH_SHISHKIN only) */
+    int device_driven;         /* 1: run the restarted FGMRES of a solve (Sec. 3.3) as one CUDA graph whose
+                                  conditional nodes take every restart, iteration and corner-cycle decision
+                                  on the device: the same kernels and results as the host-driven loop, bit
+                                  for bit, with one host synchronisation per solve instead of two or three
+                                  per iteration.  Applies to the scaled stopping rule on a capturable
+                                  stream; the graph is built at the handle's first solve of each precision
+                                  and direction and replayed afterwards.  0 (default): the host drives the
+                                  loop (measured faster on GB300, see the design notes).  The environment
+                                  variable BLP_SOLVE_GRAPH=0/1 overrides it at blp_setup. */
 } blp_params;
 
 #define BLP_MESH_SHISHKIN 0    /* piecewise-uniform layer mesh (blp_mesh) */
@@ -97,12 +106,14 @@ typedef struct {
     double relres_unscaled; /* ||f - A u||_2 / ||f||_2 (FP64) */
     double t_solve_ms;      /* wall time of the solve call */
     double t_setup_ms;      /* wall time of blp_setup for this handle */
+    int device_driven;      /* 1: the iteration ran as one CUDA graph (blp_params.device_driven);
+                               0: the host drove the loop */
 } blp_info;
 
 /* Fill *p with defaults: eps = 1e-4, N = 128, sigma = 2, beta = 1, restart
  * 30, maxit 20000, FP64, scaled stopping, corner_reduction 1e3, 50 max
  * cycles, no fixed cycles, coefficient checks on, Shishkin mesh with N/2
- * layer intervals. */
+ * layer intervals, host-driven iteration. */
 void blp_params_default(blp_params *p);
 
 /* S0. Shishkin mesh nodes (Sec. 2.2 eq. (tau 1D), Sec. 3 eq. (tau exponential)):

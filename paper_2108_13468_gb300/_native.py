@@ -26,13 +26,13 @@ class Params(ctypes.Structure):
     _fields_ = [("eps", c_double), ("N", c_int), ("sigma", c_double), ("beta_x", c_double), ("beta_y", c_double),
                 ("restart", c_int), ("maxit", c_int), ("precision", c_int), ("stop_mode", c_int),
                 ("corner_reduction", c_double), ("corner_max_cycles", c_int), ("corner_fixed_cycles", c_int),
-                ("check_coefficients", c_int), ("mesh", c_int), ("layer_intervals", c_int)]
+                ("check_coefficients", c_int), ("mesh", c_int), ("layer_intervals", c_int), ("device_driven", c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", c_int), ("iters", c_int), ("restarts", c_int), ("corner_cycles_max", c_int),
                 ("relres", c_double), ("relres_unscaled", c_double), ("t_solve_ms", c_double),
-                ("t_setup_ms", c_double)]
+                ("t_setup_ms", c_double), ("device_driven", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 #include "../../include/blp.h"
 
@@ -210,7 +211,8 @@ struct SemiHier {
 
 struct DevState {       // device scalars of the solver (double)
     double red[8];      // reduction results
-    int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[3]: running max of cycles
+    int flags[8];       // flags[0]: corner done; flags[1]: corner cycles; flags[3]: running max of cycles;
+                        // flags[4]: corner cycles run since the solve began
 };
 
 // Kernel classes for the optional event timing (blp_profile).
@@ -293,6 +295,24 @@ struct blp_handle {
     bool use_graphs = true;
     bool warm[2][2] = {{false, false}, {false, false}};   // [prec][trans]: one eager application first
     cudaStream_t own_stream = nullptr;   // capturable stream used when the caller's stream is the legacy one
+    // whole-solve graphs (device-driven FGMRES, one per [precision][direction]):
+    // every restart cycle, iteration and corner cycle is decided on the device
+    // by conditional nodes; valid while the work space stays where it was
+    struct SolveGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void *ws = nullptr;
+        int m = 0;
+        // kernels per body (restart check, restart cycle, iteration, extra
+        // corner cycle), for the launch counter
+        long long n_restart = 0, n_cycle = 0, n_iter = 0, n_corner = 0;
+    };
+    SolveGraph solve_graph[2][2];
+    bool solve_graphs = false;           // device-driven FGMRES (blp_params.device_driven, BLP_SOLVE_GRAPH)
+    cudaStream_t cap[4] = {nullptr, nullptr, nullptr, nullptr};   // body streams of nested captures
+    cudaStream_t cap_saved[4] = {nullptr, nullptr, nullptr, nullptr};
+    int cap_depth = 0;
+    bool capturing = false;              // a whole-solve capture is in progress
+    long long corner_body_launches = 0;  // kernels of one captured corner cycle body
 };
 
 // Stream-ordered device allocation from the library pool (handle's stream).
@@ -354,6 +374,74 @@ struct ProfScope {
         }                                                                     \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Conditional nodes inside a stream capture.  cap_handle creates a handle on
+// the graph that h->stream is capturing (its value is reset to `defval` at
+// every launch of the executable graph); cap_begin appends an IF or WHILE
+// node on that handle and redirects h->stream to a body stream that captures
+// the node's body graph until cap_end restores the enclosing stream.  Bodies
+// nest up to four deep.
+// ---------------------------------------------------------------------------
+static inline int cap_handle(blp_handle *h, unsigned defval, cudaGraphConditionalHandle *out) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, nullptr, nullptr, nullptr));
+    if (st != cudaStreamCaptureStatusActive || !g) return BLP_ERR_CUDA;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(out, g, defval, cudaGraphCondAssignDefault));
+    return BLP_OK;
+}
+
+static inline int cap_begin(blp_handle *h, cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type) {
+    if (h->cap_depth >= 4 || !h->cap[h->cap_depth]) return BLP_ERR_ARG;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, &deps, nullptr, &nd));
+    if (st != cudaStreamCaptureStatusActive || !g) return BLP_ERR_CUDA;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = c;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    CUDA_TRY(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t bs = h->cap[h->cap_depth];
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    h->cap_saved[h->cap_depth++] = h->stream;
+    h->stream = bs;
+    return BLP_OK;
+}
+
+static inline int cap_end(blp_handle *h) {
+    if (h->cap_depth <= 0) return BLP_ERR_ARG;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);   // the body graph belongs to its node
+    h->stream = h->cap_saved[--h->cap_depth];
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return BLP_ERR_CUDA;
+    }
+    return BLP_OK;
+}
+
+// End every capture in progress after a failure (bodies first, then the
+// outer one, whose graph is discarded) and clear the error state.
+static inline void cap_abort(blp_handle *h) {
+    while (h->cap_depth > 0) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(h->stream, &g);
+        h->stream = h->cap_saved[--h->cap_depth];
+    }
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamEndCapture(h->stream, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+}
+
 static inline int grid_for(long long n, int threads, int cap = 152 * 8) {
     long long g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
@@ -367,6 +455,9 @@ int blp_internal_ensure_ws(blp_handle *h, size_t bytes);
 int blp_internal_to_region(blp_handle *h, const double *std_in, double *reg_out, int scale_mode);
 int blp_internal_from_region(blp_handle *h, const double *reg_in, double *std_out, int scale_mode);
 template <typename T> int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles);
+// Set the kernel attributes of a preconditioner application before a
+// whole-solve capture.
+template <typename T> int precond_capture_prepare(blp_handle *h);
 // Device error flag of the handle's kernels (bounded waits): BLP_OK or the
 // recorded status, which it clears.
 int blp_internal_check_err(blp_handle *h);

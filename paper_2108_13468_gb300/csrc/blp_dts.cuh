@@ -571,16 +571,30 @@ static bool dts_attrs(K kern) {
     return true;
 }
 
+// the attributes of every form of one (precision, direction, chunk), set
+// once per process (also before a capture: attributes are not set inside one)
 template <typename T, bool REV, int CH>
-static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls, bool la) {
+static bool dts_attrs_once() {
     constexpr bool HAS_LA = CH >= 16;   // the 8-row fallback keeps the one-step form
     static std::atomic<bool> attr_set{false};
     if (!attr_set) {
         if (!dts_attrs(k_dts<T, REV, CH, false, false>) || !dts_attrs(k_dts<T, REV, CH, true, false>) ||
             (HAS_LA && !dts_attrs(k_dts<T, REV, CH, false, HAS_LA>)))
-            return BLP_ERR_CUDA;
+            return false;
         attr_set = true;
     }
+    return true;
+}
+template <typename T>
+static bool dts_attrs_all() {
+    return dts_attrs_once<T, false, 8>() && dts_attrs_once<T, false, 16>() && dts_attrs_once<T, false, 32>() &&
+           dts_attrs_once<T, true, 8>() && dts_attrs_once<T, true, 16>() && dts_attrs_once<T, true, 32>();
+}
+
+template <typename T, bool REV, int CH>
+static int launch_dts_ch(blp_handle *h, const DtsArgs<T> &a, int cls, bool la) {
+    constexpr bool HAS_LA = CH >= 16;   // the 8-row fallback keeps the one-step form
+    if (!dts_attrs_once<T, REV, CH>()) return BLP_ERR_CUDA;
     const DtsShape sh = dts_shape<T, CH>(a.R.S, h->dts_max_cluster);
     if (DtsSmem<T, CH>::bytes(sh.WC, sh.NST) > 225 * 1024) return BLP_ERR_ARG;
     // algorithmic words per node: beta, two couplings, out; the chain has one

@@ -18,11 +18,15 @@
 //   adjoint  y = x + wET x_W + wWT x_E + wNT x_S + wST x_N   ((D^-1 A)^T)
 // mode 0: out = Op x;  mode 1: out = f - Op x.  Padding slots get 0.
 // ---------------------------------------------------------------------------
+// xs != null (captured solve): also store x into column *jdev of xs.
 template <typename TC, typename TX, typename TO, bool TRANS>
 __global__ void k_matvec(Layout lay, Coefs<TC> c, const TX *__restrict__ x, TO *__restrict__ out,
-                         const TO *__restrict__ f, int mode, const double *__restrict__ rs) {
+                         const TO *__restrict__ f, int mode, const double *__restrict__ rs,
+                         TX *__restrict__ xs = nullptr, const int *jdev = nullptr) {
     const int M = lay.N - 1;
+    TX *const xcol = xs ? xs + (long long)*jdev * lay.npad : nullptr;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < lay.npad; p += (long long)gridDim.x * blockDim.x) {
+        if (xcol) xcol[p] = x[p];
         int i, j;
         if (!lay.node(p, i, j)) { out[p] = TO(0); continue; }
         TO s = (TO)x[p];
@@ -45,7 +49,9 @@ __global__ void k_matvec(Layout lay, Coefs<TC> c, const TX *__restrict__ x, TO *
 // VEC2 each thread reads two consecutive entries per vector (16-byte loads).
 template <typename T, int NV, bool VEC2>
 __global__ void __launch_bounds__(256) k_multidot(const T *__restrict__ V, long long ld, int nv,
-                                                  const T *__restrict__ w, long long n, double *partials) {
+                                                  const T *__restrict__ w, long long n, double *partials,
+                                                  const int *jdev) {
+    if (jdev) nv = *jdev + 1;   // captured solve: the basis size of the current iteration
     T acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; i++) acc[i] = T(0);
@@ -88,14 +94,15 @@ __global__ void __launch_bounds__(256) k_multidot(const T *__restrict__ V, long 
     }
 }
 
+// jdev != null: nv is the largest basis size, the kernel reads the current one
 template <typename T>
 static void launch_multidot(blp_handle *h, int nb, const T *V, long long ld, int nv, const T *w, long long n,
-                            double *partials) {
+                            double *partials, const int *jdev = nullptr) {
     const bool v2 = (ld % 2 == 0) && (n % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
 #define BLP_MD(NVB)                                                                                   \
     do {                                                                                              \
-        if (v2) k_multidot<T, NVB, true><<<nb, 256, 0, h->stream>>>(V, ld, nv, w, n, partials);      \
-        else k_multidot<T, NVB, false><<<nb, 256, 0, h->stream>>>(V, ld, nv, w, n, partials);        \
+        if (v2) k_multidot<T, NVB, true><<<nb, 256, 0, h->stream>>>(V, ld, nv, w, n, partials, jdev); \
+        else k_multidot<T, NVB, false><<<nb, 256, 0, h->stream>>>(V, ld, nv, w, n, partials, jdev);   \
     } while (0)
     if (nv <= 2) BLP_MD(2);
     else if (nv <= 4) BLP_MD(4);
@@ -107,7 +114,8 @@ static void launch_multidot(blp_handle *h, int nb, const T *V, long long ld, int
 }
 
 // out[i] = sum_b partials[b*MAXV + i] (+ add[i] if add), one warp per entry
-__global__ void k_reduce(const double *partials, int nb, int nv, double *out, const double *add) {
+__global__ void k_reduce(const double *partials, int nb, int nv, double *out, const double *add, const int *jdev) {
+    if (jdev) nv = *jdev + 1;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = threadIdx.x >> 5; i < nv; i += nw) {
         double s = 0.0;
@@ -123,7 +131,8 @@ static inline int reduce_threads(int nv) { return 32 * (nv < 32 ? nv : 32); }
 // VEC2: two consecutive entries per thread (16-byte loads and stores).
 template <typename T, int NV, bool VEC2>
 __global__ void __launch_bounds__(256) k_update(const T *__restrict__ V, long long ld, int nv, const double *__restrict__ h,
-                                                T *__restrict__ w, long long n, double *partials) {
+                                                T *__restrict__ w, long long n, double *partials, const int *jdev) {
+    if (jdev) nv = *jdev + 1;
     T hc[NV];
 #pragma unroll
     for (int i = 0; i < NV; i++) hc[i] = i < nv ? (T)h[i] : T(0);
@@ -170,12 +179,12 @@ __global__ void __launch_bounds__(256) k_update(const T *__restrict__ V, long lo
 
 template <typename T>
 static void launch_update(blp_handle *h, int nb, const T *V, long long ld, int nv, const double *hv, T *w, long long n,
-                          double *partials) {
+                          double *partials, const int *jdev = nullptr) {
     const bool v2 = (ld % 2 == 0) && (n % 2 == 0) && ((uintptr_t)V % 16 == 0) && ((uintptr_t)w % 16 == 0);
 #define BLP_UP(NVB)                                                                                   \
     do {                                                                                              \
-        if (v2) k_update<T, NVB, true><<<nb, 256, 0, h->stream>>>(V, ld, nv, hv, w, n, partials);    \
-        else k_update<T, NVB, false><<<nb, 256, 0, h->stream>>>(V, ld, nv, hv, w, n, partials);      \
+        if (v2) k_update<T, NVB, true><<<nb, 256, 0, h->stream>>>(V, ld, nv, hv, w, n, partials, jdev); \
+        else k_update<T, NVB, false><<<nb, 256, 0, h->stream>>>(V, ld, nv, hv, w, n, partials, jdev);   \
     } while (0)
     if (nv <= 2) BLP_UP(2);
     else if (nv <= 4) BLP_UP(4);
@@ -234,7 +243,8 @@ __global__ void k_scale(const TI *__restrict__ x, TO *__restrict__ y, long long 
 // u += alpha * sum_i Z_i y_i  (y on device, FP64)
 template <typename T, typename TU>
 __global__ void k_combine(const T *__restrict__ Z, long long ld, int k, const double *__restrict__ y,
-                          TU *__restrict__ u, long long n, const double *alpha_dev) {
+                          TU *__restrict__ u, long long n, const double *alpha_dev, const int *kdev) {
+    if (kdev) k = *kdev;
     __shared__ double ys[MAXV];
     const double al = alpha_dev ? *alpha_dev : 1.0;
     if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x] * al;
@@ -254,8 +264,10 @@ struct GivensState {
     double cs[MAXV], sn[MAXV], g[MAXV + 1], y[MAXV];
     double resid, hsub;
 };
-__global__ void k_givens(GivensState *G, int j, const double *h1, const double *h2, const double *nrm2) {
+__global__ void k_givens(GivensState *G, int j, const double *h1, const double *h2, const double *nrm2,
+                         const int *jdev) {
     if (threadIdx.x != 0) return;
+    if (jdev) j = *jdev;
     double col[MAXV + 1];
     for (int i = 0; i <= j; i++) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
     double hn = sqrt(*nrm2);
@@ -282,8 +294,9 @@ __global__ void k_givens_init(GivensState *G, const double *beta2) {
     G->g[0] = sqrt(*beta2);
     G->resid = G->g[0];
 }
-__global__ void k_backsolve(GivensState *G, int k) {
+__global__ void k_backsolve(GivensState *G, int k, const int *kdev) {
     if (threadIdx.x != 0) return;
+    if (kdev) k = *kdev;
     for (int i = k - 1; i >= 0; i--) {
         double s = G->g[i];
         for (int q = i + 1; q < k; q++) s -= G->H[i * MAXV + q] * G->y[q];
@@ -311,10 +324,22 @@ struct KWork {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Device control block of a captured solve (see fgmres_captured).
+struct SolveCtl {
+    double target;   // the FGMRES target for the normalised residual
+    double res;      // residual norm at the last restart
+    int fs_zero;     // zero right-hand side: nothing to solve
+    int it, maxit;   // iterations so far, iteration budget
+    int j, kdim;     // Arnoldi index and Krylov dimension of the current cycle
+    int m, restarts;
+};
+
 struct Workspace {
     KWork<double> kd;
     KWork<float> kf;
     double *u, *f, *r, *t;    // FP64 region vectors
+    void *zg;                 // captured solve: preconditioner output (either precision)
+    SolveCtl *ctl;
     bool mixed;
 };
 
@@ -329,12 +354,15 @@ static int setup_ws(blp_handle *h, Workspace &W, bool mixed) {
     size_t oV = reserve(sizeof(double) * np * (m + 2));
     size_t oZ = reserve((mixed ? sizeof(float) : sizeof(double)) * np * m);
     size_t oV32 = reserve(sizeof(float) * np);
+    size_t oZG = reserve(sizeof(double) * np), oC = reserve(sizeof(SolveCtl));
     int rc = blp_internal_ensure_ws(h, bytes);
     if (rc) return rc;
     char *base = (char *)h->ws;
     CUDA_TRY(cudaMemsetAsync(base, 0, bytes, h->stream));
     W.mixed = mixed;
     W.u = (double *)(base + oU); W.f = (double *)(base + oF); W.r = (double *)(base + oR); W.t = (double *)(base + oT);
+    W.zg = base + oZG;
+    W.ctl = (SolveCtl *)(base + oC);
     double *hb = (double *)(base + oH);
     GivensState *G = (GivensState *)(base + oG);
     double *V = (double *)(base + oV);
@@ -352,12 +380,12 @@ static int nblocks(long long np) { return (int)std::min<long long>(BLP_RED_BLOCK
 // out = Op x (mode 0) or f - Op x (mode 1); FP64 operator, x in TX precision
 template <typename TX>
 static int matvec(blp_handle *h, const TX *x, double *out, const double *f, int mode, int trans,
-                  const double *rs = nullptr) {
+                  const double *rs = nullptr, TX *xs = nullptr, const int *jdev = nullptr) {
     long long np = h->lay.npad;
     const double nodes = (double)(h->N - 1) * (h->N - 1);
     ProfScope ps(h, KC_MATVEC, nodes * (sizeof(double) * (mode ? 6 : 5) + sizeof(TX)));   // x, 4 couplings, out (+ f)
-    if (trans) k_matvec<double, TX, double, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode, rs);
-    else k_matvec<double, TX, double, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode, rs);
+    if (trans) k_matvec<double, TX, double, true><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode, rs, xs, jdev);
+    else k_matvec<double, TX, double, false><<<grid_for(np, 256), 256, 0, h->stream>>>(h->lay, h->cd, x, out, f, mode, rs, xs, jdev);
     LAUNCH_CHECK(h);
     return BLP_OK;
 }
@@ -371,7 +399,7 @@ static int norm2(blp_handle *h, const T *x, const double *scale, double *dst) {
       k_norm2<T><<<nb, 256, 0, h->stream>>>(x, np, scale, h->partials);
       LAUNCH_CHECK(h); }
     { ProfScope ps_(h, KC_SMALL);
-      k_reduce<<<1, 64, 0, h->stream>>>(h->partials, nb, 2, dst, nullptr);
+      k_reduce<<<1, 64, 0, h->stream>>>(h->partials, nb, 2, dst, nullptr, nullptr);
       LAUNCH_CHECK(h); }
     return BLP_OK;
 }
@@ -459,7 +487,7 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
               launch_multidot<double>(h, nb, K.V, np, nv, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
-              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr);
+              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
               launch_update<double>(h, nb, K.V, np, nv, h1, K.w, np, nullptr);
@@ -468,16 +496,16 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
               launch_multidot<double>(h, nb, K.V, np, nv, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
-              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr);
+              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
               launch_update<double>(h, nb, K.V, np, nv, h2, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
-              k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr);
+              k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
-              k_givens<<<1, 32, 0, h->stream>>>(K.G, j, h1, h2, nr);
+              k_givens<<<1, 32, 0, h->stream>>>(K.G, j, h1, h2, nr, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
               k_scale<double, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.w, K.V + (j + 1) * np, np, nr, 1, 1.0);
@@ -491,15 +519,260 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
             if (est <= target || hsub == 0.0) break;
         }
         { ProfScope ps_(h, KC_SMALL);
-          k_backsolve<<<1, 32, 0, h->stream>>>(K.G, kdim);
+          k_backsolve<<<1, 32, 0, h->stream>>>(K.G, kdim, nullptr);
           LAUNCH_CHECK(h); }
         { ProfScope ps_(h, KC_SMALL);
-          k_combine<TZ, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.Z, np, kdim, K.G->y, x, np, nullptr);
+          k_combine<TZ, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.Z, np, kdim, K.G->y, x, np, nullptr, nullptr);
           LAUNCH_CHECK(h); }
     }
     *iters += it;
     if (res_out) *res_out = res;
     return res <= target ? BLP_OK : BLP_ERR_NOCONV;
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven FGMRES: the whole restarted iteration as one CUDA graph.
+//
+//   WHILE (restart)                          hR: set by k_restart
+//     r = b - Op x;  beta = ||r||
+//     k_restart: stop (target met, budget spent, zero right-hand side, error)
+//     IF (cycle)                             hC: set by k_restart
+//       V_0 = r / beta;  Givens state from beta;  j = 0
+//       WHILE (iterate)                      hI: set by k_cycle_start, k_iter_end
+//         z = M^-1 V_j (corner cycles: a WHILE node of their own);
+//         w = Op z and Z_j = z;  CGS2 against V_0..V_j;  Givens;  V_j+1 = w / h
+//         k_iter_end: it++, j++; continue unless the estimate meets the
+//                     target, the Arnoldi process broke down, j = m, the
+//                     budget is spent or a kernel recorded an error
+//       x += Z y (y from the triangular solve)
+//
+// The same decisions, in the same order and with the same arithmetic, as the
+// host-driven loop in fgmres(); the host reads the control block once, after
+// the graph.  Kernels that depend on the Arnoldi index read it from the
+// control block.  The preconditioner reads and writes fixed vectors: the
+// kernel that forms V_j also writes the preconditioner's input, and the
+// operator kernel stores its input z into Z_j.  The graph touches only the
+// handle's work space, so it is built once per handle, precision and
+// direction and replayed by later solves.
+// ---------------------------------------------------------------------------
+__global__ void k_ctl_init(SolveCtl *c, double target, int fs_zero, int maxit, int m) {
+    c->target = target;
+    c->res = 0.0;
+    c->fs_zero = fs_zero;
+    c->it = 0;
+    c->maxit = maxit;
+    c->j = 0;
+    c->kdim = 0;
+    c->m = m;
+    c->restarts = 0;
+}
+
+__global__ void k_restart(SolveCtl *c, const double *beta2, const int *err, cudaGraphConditionalHandle hR,
+                          cudaGraphConditionalHandle hC) {
+    const double res = sqrt(*beta2);
+    c->res = res;
+    const bool stop = c->fs_zero || res <= c->target || c->it >= c->maxit || *err != 0;
+    if (!stop) c->restarts++;
+    c->j = 0;
+    c->kdim = 0;
+    cudaGraphSetConditional(hR, stop ? 0u : 1u);
+    cudaGraphSetConditional(hC, stop ? 0u : 1u);
+}
+
+__global__ void k_cycle_start(GivensState *G, const double *beta2, cudaGraphConditionalHandle hI) {
+    for (int i = 0; i <= MAXV; i++) G->g[i] = 0.0;
+    G->g[0] = sqrt(*beta2);
+    G->resid = G->g[0];
+    cudaGraphSetConditional(hI, 1u);
+}
+
+// V_0 = r / ||r|| in place, and the preconditioner's input (V_0 in its precision)
+template <typename TO>
+__global__ void k_scale_first(double *__restrict__ V, long long np, const double *beta2, TO *__restrict__ vin) {
+    const double s = sqrt(*beta2);
+    const double f = s != 0.0 ? 1.0 / s : 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
+        const double v = V[k] * f;
+        V[k] = v;
+        vin[k] = (TO)v;
+    }
+}
+
+// V_{j+1} = w / sqrt(nrm2), and the next preconditioner input
+template <typename TO>
+__global__ void k_scale_col(const int *jdev, const double *__restrict__ w, double *__restrict__ V, long long np,
+                            const double *nrm2, TO *__restrict__ vin) {
+    const double s = sqrt(*nrm2);
+    const double f = s != 0.0 ? 1.0 / s : 0.0;
+    double *v = V + (long long)(*jdev + 1) * np;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
+        const double x = w[k] * f;
+        v[k] = x;
+        vin[k] = (TO)x;
+    }
+}
+
+__global__ void k_iter_end(SolveCtl *c, const GivensState *G, const int *err, cudaGraphConditionalHandle hI) {
+    c->it++;
+    c->j++;
+    c->kdim = c->j;
+    const bool stop = G->resid <= c->target || G->hsub == 0.0 || c->j >= c->m || c->it >= c->maxit || *err != 0;
+    cudaGraphSetConditional(hI, stop ? 0u : 1u);
+}
+
+// The preconditioner's input vector of the captured solve: the FP32 copy of
+// the basis vector (mixed) or an FP64 scratch vector.
+template <typename TZ>
+static TZ *precond_input(Workspace &W, KWork<TZ> &K) {
+    return sizeof(TZ) == 4 ? reinterpret_cast<TZ *>(K.v32) : reinterpret_cast<TZ *>(W.t);
+}
+
+// One Arnoldi step with Z_j = M^-1 V_j, j read from the control block.
+template <typename TZ>
+static int capture_iteration(blp_handle *h, Workspace &W, KWork<TZ> &K, int trans, cudaGraphConditionalHandle hI) {
+    const long long np = K.np;
+    const int m = K.m, nb = nblocks(np);
+    const int *jdev = &W.ctl->j;
+    TZ *vin = precond_input<TZ>(W, K);   // V_j, written when V_j was formed
+    TZ *zg = static_cast<TZ *>(W.zg);
+    double *h1 = K.hbuf, *h2 = K.hbuf + MAXV, *nr = K.hbuf + 2 * MAXV;
+    int rc, cyc = 0;
+    if ((rc = precond_apply<TZ>(h, vin, zg, trans, &cyc))) return rc;
+    if ((rc = matvec<TZ>(h, zg, K.w, nullptr, 0, trans, nullptr, K.Z, jdev))) return rc;   // and Z_j = z
+    launch_multidot<double>(h, nb, K.V, np, m, K.w, np, h->partials, jdev);
+    LAUNCH_CHECK(h);
+    k_reduce<<<1, reduce_threads(m), 0, h->stream>>>(h->partials, nb, m, h1, nullptr, jdev);
+    LAUNCH_CHECK(h);
+    launch_update<double>(h, nb, K.V, np, m, h1, K.w, np, nullptr, jdev);
+    LAUNCH_CHECK(h);
+    launch_multidot<double>(h, nb, K.V, np, m, K.w, np, h->partials, jdev);
+    LAUNCH_CHECK(h);
+    k_reduce<<<1, reduce_threads(m), 0, h->stream>>>(h->partials, nb, m, h2, nullptr, jdev);
+    LAUNCH_CHECK(h);
+    launch_update<double>(h, nb, K.V, np, m, h2, K.w, np, h->partials, jdev);
+    LAUNCH_CHECK(h);
+    k_reduce<<<1, 32, 0, h->stream>>>(h->partials, nb, 1, nr, nullptr, nullptr);
+    LAUNCH_CHECK(h);
+    k_givens<<<1, 32, 0, h->stream>>>(K.G, 0, h1, h2, nr, jdev);
+    LAUNCH_CHECK(h);
+    k_scale_col<TZ><<<grid_for(np, 256), 256, 0, h->stream>>>(jdev, K.w, K.V, np, nr, vin);
+    LAUNCH_CHECK(h);
+    k_iter_end<<<1, 1, 0, h->stream>>>(W.ctl, K.G, h->err, hI);
+    LAUNCH_CHECK(h);
+    return BLP_OK;
+}
+
+struct CapturedCounts { long long restart, cycle, iter; };
+
+template <typename TZ>
+static int capture_solve(blp_handle *h, Workspace &W, KWork<TZ> &K, int trans, CapturedCounts *cnt) {
+    const long long np = K.np;
+    int rc;
+    cudaGraphConditionalHandle hR, hC, hI;
+    const long long l0 = h->launches;
+    if ((rc = cap_handle(h, 1, &hR))) return rc;
+    if ((rc = cap_begin(h, hR, cudaGraphCondTypeWhile))) return rc;
+    {
+        const long long l1 = h->launches;
+        if ((rc = matvec<double>(h, W.u, K.V, W.f, 1, trans))) return rc;
+        if ((rc = norm2<double>(h, K.V, nullptr, K.hbuf + 3 * MAXV))) return rc;
+        if ((rc = cap_handle(h, 0, &hC))) return rc;
+        k_restart<<<1, 1, 0, h->stream>>>(W.ctl, K.hbuf + 3 * MAXV, h->err, hR, hC);
+        LAUNCH_CHECK(h);
+        cnt->restart = h->launches - l1;
+        if ((rc = cap_begin(h, hC, cudaGraphCondTypeIf))) return rc;
+        {
+            const long long l2 = h->launches;
+            k_scale_first<TZ><<<grid_for(np, 256), 256, 0, h->stream>>>(K.V, np, K.hbuf + 3 * MAXV, precond_input<TZ>(W, K));
+            LAUNCH_CHECK(h);
+            if ((rc = cap_handle(h, 0, &hI))) return rc;
+            k_cycle_start<<<1, 1, 0, h->stream>>>(K.G, K.hbuf + 3 * MAXV, hI);
+            LAUNCH_CHECK(h);
+            if ((rc = cap_begin(h, hI, cudaGraphCondTypeWhile))) return rc;
+            const long long l3 = h->launches;
+            rc = capture_iteration<TZ>(h, W, K, trans, hI);
+            cnt->iter = h->launches - l3;
+            if (rc) return rc;
+            if ((rc = cap_end(h))) return rc;
+            k_backsolve<<<1, 32, 0, h->stream>>>(K.G, 0, &W.ctl->kdim);
+            LAUNCH_CHECK(h);
+            k_combine<TZ, double><<<grid_for(np, 256), 256, 0, h->stream>>>(K.Z, np, 0, K.G->y, W.u, np, nullptr,
+                                                                           &W.ctl->kdim);
+            LAUNCH_CHECK(h);
+            cnt->cycle = h->launches - l2 - cnt->iter;
+        }
+        if ((rc = cap_end(h))) return rc;
+    }
+    if ((rc = cap_end(h))) return rc;
+    h->launches = l0;   // counted when the graph runs
+    return BLP_OK;
+}
+
+static_assert(sizeof(SolveCtl) <= sizeof(DevState::red), "the control block is read back through host_state->red");
+
+// Run the captured solve (building its graph on first use).  Adds the
+// iterations and restarts the device took; the caller forms the residuals.
+// *fallback is set when the graph cannot be built (nothing was launched):
+// the caller then runs the host-driven loop instead.
+template <typename TZ>
+static int fgmres_captured(blp_handle *h, Workspace &W, KWork<TZ> &K, int trans, double target, bool fs_zero,
+                           int maxit, int *iters, int *restarts, bool *fallback) {
+    *fallback = false;
+    const int prec = sizeof(TZ) == 4 ? 1 : 0;
+    blp_handle::SolveGraph &SG = h->solve_graph[prec][trans ? 1 : 0];
+    if (SG.exec && (SG.ws != h->ws || SG.m != K.m)) {
+        cudaGraphExecDestroy(SG.exec);
+        SG.exec = nullptr;
+    }
+    if (!SG.exec) {
+        *fallback = true;
+        int rc = precond_capture_prepare<TZ>(h);
+        if (rc) return rc;
+        for (int q = 0; q < 4; q++)
+            if (!h->cap[q]) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap[q], cudaStreamNonBlocking));
+        CapturedCounts cnt = {0, 0, 0};
+        h->corner_body_launches = 0;
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        rc = capture_solve<TZ>(h, W, K, trans, &cnt);
+        h->capturing = false;
+        if (rc) {
+            cap_abort(h);
+            return rc;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&SG.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            SG.exec = nullptr;
+            return BLP_ERR_CUDA;
+        }
+        SG.ws = h->ws;
+        SG.m = K.m;
+        SG.n_restart = cnt.restart;
+        SG.n_cycle = cnt.cycle;
+        SG.n_iter = cnt.iter;
+        SG.n_corner = h->corner_body_launches;
+        *fallback = false;
+    }
+    k_ctl_init<<<1, 1, 0, h->stream>>>(W.ctl, target, fs_zero ? 1 : 0, maxit, K.m);
+    LAUNCH_CHECK(h);
+    CUDA_TRY(cudaGraphLaunch(SG.exec, h->stream));
+    SolveCtl c;
+    CUDA_TRY(cudaMemcpyAsync(h->host_state->red, W.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&h->host_state->flags[4], &h->dev->flags[4], sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    memcpy(&c, h->host_state->red, sizeof(SolveCtl));
+    *iters += c.it;
+    *restarts += c.restarts;
+    // kernels the graph ran: one restart body per restart plus the final
+    // check, one cycle body per restart, one iteration body per iteration,
+    // and the corner cycles beyond the first of each application
+    const long long extra_cycles = std::max(0LL, (long long)h->host_state->flags[4] - c.it);
+    h->launches += SG.n_restart * (c.restarts + 1) + SG.n_cycle * c.restarts + SG.n_iter * c.it + SG.n_corner * extra_cycles;
+    return BLP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -548,7 +821,7 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     double target_scaled = mode == BLP_STOP_SCALED ? tol * fs : 0.0;
     double target_unscaled = mode == BLP_STOP_REL2 ? tol * fu : (mode == BLP_STOP_ABS2 ? tol : 0.0);
 
-    int iters = 0, restarts = 0, maxcyc = 0, status = BLP_ERR_NOCONV;
+    int iters = 0, restarts = 0, maxcyc = 0, status = BLP_ERR_NOCONV, device_driven = 0;
     double res_s = 0.0, res_u = 0.0;
     // true residuals of the current u in both norms
     auto true_res = [&](double &rs, double &ru) -> int {
@@ -565,7 +838,7 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
     auto met = [&](double rs, double ru) {
         return mode == BLP_STOP_SCALED ? rs <= target_scaled : ru <= target_unscaled;
     };
-    CUDA_TRY(cudaMemsetAsync(&h->dev->flags[3], 0, sizeof(int), h->stream));
+    CUDA_TRY(cudaMemsetAsync(&h->dev->flags[3], 0, 2 * sizeof(int), h->stream));   // flags[3], flags[4]
     if ((rc = true_res(res_s, res_u))) return rc;
     if (fs == 0.0) {
         status = BLP_OK;
@@ -577,7 +850,25 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
         // path use D^-1 A: an FP32 preconditioner fed D^-1 v for unscaled v
         // (entries spanning the diagonal's ~1e11 range) loses the layer rows.
         const double *rs = (!trans && !mixed && mode != BLP_STOP_SCALED) ? h->aC : nullptr;
-        while (!met(res_s, res_u) && iters < budget) {
+        // device-driven iteration (one graph launch) under the scaled rule
+        bool host_loop = true;
+        if (h->solve_graphs && h->use_graphs && h->stream != 0 && !h->prof.on && mode == BLP_STOP_SCALED &&
+            !met(res_s, res_u)) {
+            bool fallback = false;
+            if (mixed) rc = fgmres_captured<float>(h, W, W.kf, trans, target_scaled, false, budget, &iters, &restarts, &fallback);
+            else rc = fgmres_captured<double>(h, W, W.kd, trans, target_scaled, false, budget, &iters, &restarts, &fallback);
+            if (fallback) {
+                h->solve_graphs = false;   // this handle keeps the host-driven loop
+            } else {
+                if (rc) return rc;
+                if ((rc = true_res(res_s, res_u))) return rc;
+                host_loop = false;
+                device_driven = 1;
+                // the host-driven loop counts fixed corner cycles on the host
+                if (h->p.corner_fixed_cycles > 0 && iters > 0) maxcyc = std::max(maxcyc, h->p.corner_fixed_cycles);
+            }
+        }
+        while (host_loop && !met(res_s, res_u) && iters < budget) {
             // without rs the Arnoldi estimate tracks the normalised residual:
             // for the unscaled rules convert the target with the current ratio
             double tgt = mode == BLP_STOP_SCALED ? target_scaled
@@ -615,6 +906,7 @@ static int solve_common(blp_handle *h, const double *f_in, double *u_io, double 
                                                : (mode == BLP_STOP_REL2 ? (fu > 0 ? res_u / fu : 0.0) : res_u);
         info->relres_unscaled = fu > 0 ? res_u / fu : 0.0;
         info->t_setup_ms = h->t_setup_ms;
+        info->device_driven = device_driven;
         info->t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     return status;

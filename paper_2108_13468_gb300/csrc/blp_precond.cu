@@ -484,19 +484,26 @@ int blp_internal_chain_pre(blp_handle *h) { return chain_pre_one<double>(h, h->c
 // FP64 chains use the precomputed multipliers (the FP64 scans are bound by one
 // SM's FP64 FMA rate); FP32 chains, bound by latency, form them on the fly.
 template <typename T, int KPT, int NW, int NS, bool TRANS>
-static int launch_chain2(blp_handle *h, const ChainArgs<T> &a) {
+static bool chain2_attrs_once() {
     constexpr bool USEPRE = sizeof(T) == 8;
-    constexpr size_t smem = NS * ChainSmem<T, KPT, NW, USEPRE>::stage;
-    static_assert(smem <= 225 * 1024, "line-chain stages exceed the shared-memory budget");
     static std::atomic<bool> attr_set{false};
     if (!attr_set) {
         if (cudaFuncSetAttribute(k_line_chain2<T, KPT, NW, NS, TRANS, USEPRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  225 * 1024) != cudaSuccess) {
             cudaGetLastError();
-            return BLP_ERR_CUDA;
+            return false;
         }
         attr_set = true;
     }
+    return true;
+}
+
+template <typename T, int KPT, int NW, int NS, bool TRANS>
+static int launch_chain2(blp_handle *h, const ChainArgs<T> &a) {
+    constexpr bool USEPRE = sizeof(T) == 8;
+    constexpr size_t smem = NS * ChainSmem<T, KPT, NW, USEPRE>::stage;
+    static_assert(smem <= 225 * 1024, "line-chain stages exceed the shared-memory budget");
+    if (!chain2_attrs_once<T, KPT, NW, NS, TRANS>()) return BLP_ERR_CUDA;
     k_line_chain2<T, KPT, NW, NS, TRANS, USEPRE><<<2, 32 * NW, smem, h->stream>>>(a);
     LAUNCH_CHECK(h);
     return BLP_OK;
@@ -688,9 +695,16 @@ __global__ void k_corner_norm(Level<T> Lv, const T *__restrict__ b, const T *__r
 // a rounding floor near 2^-24 || |A| |e| ||, which on a fine, diffusion-
 // dominated corner (eps N >> 1) lies above the 1e3 reduction; the V-cycle
 // contracts by far more than stall2 per cycle until it reaches that floor.
+// When the iteration stops, flags[3] keeps the largest cycle count so far;
+// flags[4] counts the cycles run since the solve began.
+// use_cond: inside a captured solve, the conditional of the WHILE node that
+// repeats the cycles is set to "not done" (an error flag also ends it).
 __global__ void k_corner_finish(double *partials, int nb, DevState *st, int mode, double red2, int maxc,
-                                double stall2) {
-    if (st->flags[0] && mode == 1) return;
+                                double stall2, cudaGraphConditionalHandle cond, int use_cond, const int *err) {
+    if (st->flags[0] && mode == 1) {
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) s += partials[i];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(FULL, s, off);
@@ -701,9 +715,12 @@ __global__ void k_corner_finish(double *partials, int nb, DevState *st, int mode
             st->flags[1] = 0;
         } else {
             st->flags[1] += 1;
+            st->flags[4] += 1;
             if (s <= st->red[0] || st->flags[1] >= maxc || (stall2 > 0.0 && s > stall2 * st->red[2])) st->flags[0] = 1;
+            if (st->flags[0]) atomicMax(&st->flags[3], st->flags[1]);
         }
         st->red[2] = s;
+        if (use_cond) cudaGraphSetConditional(cond, (st->flags[0] || (err && *err)) ? 0 : 1);
     }
 }
 
@@ -1139,6 +1156,21 @@ static int coarse_start(const Hierarchy<T> &H) {
 }
 
 template <typename T, bool TRANS>
+static bool coarse_attrs_once() {
+    static std::atomic<bool> attr{false};
+    if (!attr) {
+        // dynamic bytes this kernel ever asks for (coarse_start caps them at 200 KB); it also
+        // has a little static shared memory, so the opt-in maximum itself would be rejected
+        if (cudaFuncSetAttribute(k_mg_coarse<T, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        attr = true;
+    }
+    return true;
+}
+
+template <typename T, bool TRANS>
 static int launch_coarse(blp_handle *h, Hierarchy<T> &H, int l0, const T *b_in, T *e_out, int full, const int *skip) {
     CoarseArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -1149,16 +1181,7 @@ static int launch_coarse(blp_handle *h, Hierarchy<T> &H, int l0, const T *b_in, 
     a.red2 = h->p.corner_reduction * h->p.corner_reduction;
     a.st = h->dev; a.skip = skip; a.err = h->err;
     const size_t smem = coarse_smem(H, l0);
-    static std::atomic<bool> attr{false};
-    if (!attr) {
-        // dynamic bytes this kernel ever asks for (coarse_start caps them at 200 KB); it also
-        // has a little static shared memory, so the opt-in maximum itself would be rejected
-        if (cudaFuncSetAttribute(k_mg_coarse<T, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
-            cudaGetLastError();
-            return BLP_ERR_CUDA;
-        }
-        attr = true;
-    }
+    if (!coarse_attrs_once<T, TRANS>()) return BLP_ERR_CUDA;
     double bytes = 0.0;
     for (int l = l0; l < H.nlev; l++) bytes += 14.0 * sizeof(T) * H.lev[l].R.mx * H.lev[l].R.mx;
     ProfScope ps(h, KC_MG_COARSE, bytes);
@@ -1263,7 +1286,7 @@ static int corner_more(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int cou
         k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[cy.cur[0]], 1, h->partials, done);
         LAUNCH_CHECK(h);
         k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles,
-                                                 corner_stall2<T>());
+                                                 corner_stall2<T>(), 0, 0, nullptr);
         LAUNCH_CHECK(h);
     }
     return BLP_OK;
@@ -1285,7 +1308,7 @@ static int corner_front(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int ba
         k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
         LAUNCH_CHECK(h);
         k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles,
-                                                 corner_stall2<T>());
+                                                 corner_stall2<T>(), 0, 0, nullptr);
         LAUNCH_CHECK(h);
     }
     cy.skip = done;
@@ -1304,6 +1327,57 @@ static int corner_rest(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, int *en
     }
     *cycles = h->host_state->flags[1];
     h->last_cycles = *cycles + 1;
+    return BLP_OK;
+}
+
+// Inside a captured solve: the first cycle (from e = 0), then a WHILE node
+// whose body is one more cycle with its stopping test; every test sets the
+// node's conditional, so the cycles repeat on the device until the test
+// passes or the cycle cap is reached.  One cycle leaves every level's
+// iterate in the buffer it started in, so all cycles are the same body.
+template <typename T, bool TRANS>
+static int corner_solve_captured(blp_handle *h, const T *b0, Cycler<T, TRANS> &cy, T **result) {
+    Hierarchy<T> &H = hier_of<T>(h);
+    Level<T> &L0 = H.lev[0];
+    const int nb = BLP_RED_BLOCKS;
+    const double red2 = h->p.corner_reduction * h->p.corner_reduction;
+    int *done = h->dev->flags;
+    int rc;
+    for (int l = 0; l < H.nlev; l++) { cy.cur[l] = 0; cy.zero[l] = false; }
+    cy.zero[0] = true;
+    CUDA_TRY(cudaMemsetAsync(L0.e[0], 0, sizeof(T) * L0.R.size, h->stream));
+    cy.skip = nullptr;
+    k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[0], 0, h->partials, nullptr);
+    LAUNCH_CHECK(h);
+    k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles,
+                                             corner_stall2<T>(), 0, 0, nullptr);
+    LAUNCH_CHECK(h);
+    cy.skip = done;
+    cudaGraphConditionalHandle cond;
+    if ((rc = cap_handle(h, 0, &cond))) return rc;
+    auto cycle = [&]() -> int {
+        int r2 = cy.vcycle(0);
+        if (r2) return r2;
+        k_corner_norm<T, TRANS><<<nb, 256, 0, h->stream>>>(L0, b0, L0.e[cy.cur[0]], 1, h->partials, done);
+        LAUNCH_CHECK(h);
+        k_corner_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles,
+                                                 corner_stall2<T>(), cond, 1, h->err);
+        LAUNCH_CHECK(h);
+        return BLP_OK;
+    };
+    if ((rc = cycle())) return rc;
+    int cur0[BLP_MAXLEV];
+    for (int l = 0; l < H.nlev; l++) cur0[l] = cy.cur[l];
+    if ((rc = cap_begin(h, cond, cudaGraphCondTypeWhile))) return rc;
+    const long long l0 = h->launches;
+    rc = cycle();
+    h->corner_body_launches = h->launches - l0;
+    const int rc2 = cap_end(h);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    for (int l = 0; l < H.nlev; l++)
+        if (cy.cur[l] != cur0[l]) return BLP_ERR_ARG;   // a cycle must end where it began
+    *result = L0.e[cy.cur[0]];
     return BLP_OK;
 }
 
@@ -1330,6 +1404,10 @@ static int corner_solve(blp_handle *h, const T *b0, T **result, int *cycles_out)
         cy.skip = nullptr;
         for (int c = 0; c < fixed; c++) { int rc = cy.vcycle(0); if (rc) return rc; }
         cycles = fixed;
+    } else if (h->capturing) {
+        int rc = corner_solve_captured<T, TRANS>(h, b0, cy, result);
+        if (cycles_out) *cycles_out = -1;
+        return rc;
     } else {
         int enq = 0, rc;
         const int batch = std::max(2, std::min(h->last_cycles > 0 ? h->last_cycles : 6, h->p.corner_max_cycles));
@@ -1470,10 +1548,10 @@ template <typename T>
 int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles) {
     const int prec = sizeof(T) == 4 ? 1 : 0;
     if (h->semi && trans) return BLP_ERR_ARG;   // the parabolic-layer corner cycle is forward only
-    if (h->use_graphs && h->warm[prec][trans ? 1 : 0] && h->stream != 0 && !h->prof.on &&
+    if (h->use_graphs && h->warm[prec][trans ? 1 : 0] && h->stream != 0 && !h->prof.on && !h->capturing &&
         h->p.corner_fixed_cycles <= 0 && coarse_start(hier_of<T>(h)) > 0 && !h->semi)
         return precond_graph<T>(h, v, z, trans, cycles);
-    h->warm[prec][trans ? 1 : 0] = true;   // the first application runs eagerly (kernel attributes set outside any capture)
+    if (!h->capturing) h->warm[prec][trans ? 1 : 0] = true;   // the first application runs eagerly (kernel attributes set outside any capture)
     Coefs<T> &c = coefs_of<T>(h);
     Hierarchy<T> &H = hier_of<T>(h);
     const Layout &lay = h->lay;
@@ -1519,3 +1597,20 @@ int precond_apply(blp_handle *h, const T *v, T *z, int trans, int *cycles) {
 
 template int precond_apply<double>(blp_handle *, const double *, double *, int, int *);
 template int precond_apply<float>(blp_handle *, const float *, float *, int, int *);
+
+// Kernel attributes of everything one application can launch, set before a
+// whole-solve capture begins (no attribute is set inside a capture).
+template <typename T>
+int precond_capture_prepare(blp_handle *h) {
+    if (!dts_attrs_all<T>() || !coarse_attrs_once<T, false>() || !coarse_attrs_once<T, true>()) return BLP_ERR_CUDA;
+    if (chain2_applies(h, sizeof(T))) {
+        const bool ok = with_chain_cfg<T>(h->L, [&](auto cfg) -> int {
+            using C = decltype(cfg);
+            return chain2_attrs_once<T, C::KPT, C::NW, C::NS, false>() && chain2_attrs_once<T, C::KPT, C::NW, C::NS, true>();
+        });
+        if (!ok) return BLP_ERR_CUDA;
+    }
+    return BLP_OK;
+}
+template int precond_capture_prepare<double>(blp_handle *);
+template int precond_capture_prepare<float>(blp_handle *);

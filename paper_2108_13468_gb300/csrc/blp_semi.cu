@@ -360,10 +360,16 @@ __global__ void k_semi_norm(SemiLev<T> L, int mode, double *partials, const int 
 // mode 1: flags[1]++, flags[0] = 1 once ||r||^2 <= red[0] or the cycle cap is
 // reached, or (stall2 > 0, FP32) once a cycle leaves ||r||^2 above stall2
 // times the previous one's (red[2]): the rounding floor of an FP32 iterate
-// can lie above the requested reduction.
+// can lie above the requested reduction.  flags[3] keeps the largest cycle
+// count, flags[4] counts the cycles run.  use_cond: inside a captured solve,
+// the conditional of the WHILE node that repeats the cycles is set to
+// "not done" (an error flag also ends it).
 __global__ void k_semi_finish(const double *partials, int nb, DevState *st, int mode, double red2, int maxc,
-                              double stall2) {
-    if (mode == 1 && st->flags[0]) return;
+                              double stall2, cudaGraphConditionalHandle cond, int use_cond, const int *err) {
+    if (mode == 1 && st->flags[0]) {
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) s += partials[i];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(SFULL, s, off);
@@ -374,9 +380,12 @@ __global__ void k_semi_finish(const double *partials, int nb, DevState *st, int 
             st->flags[1] = 0;
         } else {
             st->flags[1] += 1;
+            st->flags[4] += 1;
             if (s <= st->red[0] || st->flags[1] >= maxc || (stall2 > 0.0 && s > stall2 * st->red[2])) st->flags[0] = 1;
+            if (st->flags[0]) atomicMax(&st->flags[3], st->flags[1]);
         }
         st->red[2] = s;
+        if (use_cond) cudaGraphSetConditional(cond, (st->flags[0] || (err && *err)) ? 0 : 1);
     }
 }
 
@@ -449,7 +458,7 @@ struct SemiCycler {
 };
 
 template <typename T>
-int cycle_and_test(blp_handle *h, SemiCycler<T> &cy, bool first) {
+int cycle_and_test(blp_handle *h, SemiCycler<T> &cy, bool first, cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
     SemiLev<T> &L0 = cy.H->lev[0];
     STRY(cy.vcycle(0, first));
     const long long n = (long long)L0.sx * L0.m;
@@ -459,7 +468,7 @@ int cycle_and_test(blp_handle *h, SemiCycler<T> &cy, bool first) {
     LAUNCH_CHECK(h);
     const double red2 = h->p.corner_reduction * h->p.corner_reduction;
     k_semi_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 1, red2, h->p.corner_max_cycles,
-                                           sizeof(T) == 4 ? 0.25 : 0.0);
+                                           sizeof(T) == 4 ? 0.25 : 0.0, cond, use_cond, h->err);
     LAUNCH_CHECK(h);
     return BLP_OK;
 }
@@ -577,24 +586,41 @@ int semi_corner_solve(blp_handle *h, const T *b0, T *out, int *cycles_out) {
             ProfScope ps(h, KC_CORNER_NORM, (double)n0 * sizeof(T));
             k_semi_norm<T><<<nb, 256, 0, h->stream>>>(L0, 0, h->partials, nullptr);
             LAUNCH_CHECK(h);
-            k_semi_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles, 0.0);
+            k_semi_finish<<<1, 32, 0, h->stream>>>(h->partials, nb, h->dev, 0, red2, h->p.corner_max_cycles, 0.0,
+                                                   0, 0, nullptr);
             LAUNCH_CHECK(h);
         }
         // a batch of cycles (the count the last application needed) with the
         // stopping test on the device, then more while the test fails
         cy.skip = h->dev->flags;
-        int enq = 0;
-        const int batch = std::max(1, std::min(h->last_cycles > 0 ? h->last_cycles : 3, h->p.corner_max_cycles));
-        for (; enq < batch; enq++) STRY(cycle_and_test<T>(h, cy, enq == 0));
-        for (;;) {
-            CUDA_TRY(cudaMemcpyAsync(h->host_state, h->dev, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
-            CUDA_TRY(cudaStreamSynchronize(h->stream));
-            if (h->host_state->flags[0] || enq >= h->p.corner_max_cycles) break;
-            STRY(cycle_and_test<T>(h, cy, false));
-            enq++;
+        if (h->capturing) {
+            // captured solve: the first cycle, then a WHILE node repeating one
+            // more cycle while the stopping test fails (the cycle is in place)
+            cudaGraphConditionalHandle cond;
+            STRY(cap_handle(h, 0, &cond));
+            STRY(cycle_and_test<T>(h, cy, true, cond, 1));
+            STRY(cap_begin(h, cond, cudaGraphCondTypeWhile));
+            const long long l0 = h->launches;
+            const int rc = cycle_and_test<T>(h, cy, false, cond, 1);
+            h->corner_body_launches = h->launches - l0;
+            const int rc2 = cap_end(h);
+            if (rc) return rc;
+            if (rc2) return rc2;
+            cycles = -1;
+        } else {
+            int enq = 0;
+            const int batch = std::max(1, std::min(h->last_cycles > 0 ? h->last_cycles : 3, h->p.corner_max_cycles));
+            for (; enq < batch; enq++) STRY(cycle_and_test<T>(h, cy, enq == 0));
+            for (;;) {
+                CUDA_TRY(cudaMemcpyAsync(h->host_state, h->dev, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+                CUDA_TRY(cudaStreamSynchronize(h->stream));
+                if (h->host_state->flags[0] || enq >= h->p.corner_max_cycles) break;
+                STRY(cycle_and_test<T>(h, cy, false));
+                enq++;
+            }
+            cycles = h->host_state->flags[1];
+            h->last_cycles = cycles;
         }
-        cycles = h->host_state->flags[1];
-        h->last_cycles = cycles;
     }
     {
         ProfScope ps(h, KC_LAYOUT);

@@ -395,6 +395,11 @@ extern "C" void blp_destroy(blp_handle *h) {
     for (auto &e : h->prof.ev) cudaEventDestroy(e);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    for (auto &row : h->solve_graph)
+        for (auto &g : row)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaStream_t &cs : h->cap)
+        if (cs) cudaStreamDestroy(cs);
     for (int q = 0; q < 2; q++) { blp_internal_free(h, h->gv[q]); blp_internal_free(h, h->gz[q]); }
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     void *ps[] = {h->x, h->y, h->aC, h->c1, h->c2, h->r, h->partials, h->dev, h->err, h->ws,
@@ -727,6 +732,8 @@ int blp_internal_setup(const blp_params *p, const double *c1, const double *c2, 
         h->dts_chunk = (c == 8 || c == 16 || c == 32) ? c : 0;
     }
     if (const char *e = getenv("BLP_GRAPHS")) h->use_graphs = atoi(e) != 0;
+    h->solve_graphs = p->device_driven != 0;
+    if (const char *e = getenv("BLP_SOLVE_GRAPH")) h->solve_graphs = atoi(e) != 0;
     h->stream = stream;
     int rc = setup_impl(h, c1, c2, r);
     if (rc != BLP_OK) {

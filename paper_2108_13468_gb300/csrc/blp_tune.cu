@@ -41,11 +41,15 @@ void apply(blp_handle *h, const blp_tuning &t) {
     const bool same = h->dts_chunk == t.dts_chunk && h->dts_max_cluster == t.dts_cluster &&
                       h->dts_two_step32 == ((t.two_step & 1) != 0) && h->dts_two_step64 == ((t.two_step & 2) != 0);
     if (same) return;
-    if (!h->graphs.empty()) {
-        cudaStreamSynchronize(h->stream);
-        for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
-        h->graphs.clear();
-    }
+    cudaStreamSynchronize(h->stream);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    for (auto &row : h->solve_graph)
+        for (auto &g : row)
+            if (g.exec) {
+                cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+            }
     for (auto &w : h->warm) w[0] = w[1] = false;
     h->dts_chunk = t.dts_chunk;
     h->dts_max_cluster = t.dts_cluster;
