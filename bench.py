@@ -468,7 +468,7 @@ def leg_batched(blp, torch, dev):
 
     def batched(tuned):
         items = [dict(q, precision=blp.BLP_MIXED, maxit=3000, u=torch.zeros_like(q["f"])) for q in probs]
-        res = blp.solve_batched(items, tol=TOL, concurrency=8, autotune=tuned)
+        res = blp.solve_batched(items, tol=TOL, concurrency=16, autotune=tuned)
         return max(info.relres for _, info in res)
 
     def one_at_a_time():

@@ -206,7 +206,7 @@ typedef struct {
 
 /* Solve `count` independent problems (Sec. 3.3 solve of each; the batched
  * workload of many small problems with different N and eps).  Up to
- * `concurrency` problems (<= 0: 8) are in flight at once, each on its own
+ * `concurrency` problems (<= 0: 16) are in flight at once, each on its own
  * stream of the current device, set up, solved and released by one of
  * `concurrency` host threads.  Per-problem conventions are those of
  * blp_setup + blp_solve; items[i].status and items[i].info report each

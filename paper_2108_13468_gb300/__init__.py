@@ -194,7 +194,7 @@ class Solver:
         return t.as_dict()
 
 
-def solve_batched(problems, tol=1e-10, concurrency=8, autotune=False):
+def solve_batched(problems, tol=1e-10, concurrency=16, autotune=False):
     """blp_solve_batched: independent problems solved concurrently.
 
     problems: list of dicts with keys N, eps, c1, c2, r, f (float64 arrays or

@@ -76,7 +76,7 @@ static int solve_batched(blp_batch_item *items, int count, int concurrency, bool
         cudaStreamDestroy(ts);
     }
     for (int i = 0; i < count; i++) items[i].status = -1;
-    const int K = std::max(1, std::min(concurrency > 0 ? concurrency : 8, count));
+    const int K = std::max(1, std::min(concurrency > 0 ? concurrency : 16, count));
     std::atomic<int> next{0};
     std::vector<std::thread> pool;
     try {
