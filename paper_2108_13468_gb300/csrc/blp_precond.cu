@@ -109,6 +109,8 @@ __device__ __forceinline__ void scan_multipliers(const T (&mu)[KPT], T (&pre)[7]
     pre[6] = BACK ? __shfl_down_sync(FULL, M, 1) : __shfl_up_sync(FULL, M, 1);
 }
 
+// sh: 64 values of shared memory, not the buffer of the scan just before
+// (the warp totals of a scan stay readable until the scan after next).
 template <typename T, int KPT, bool BACK>
 __device__ __forceinline__ void block_affine_scan_pre(const T (&al)[KPT], const T (&mu)[KPT], const T (&pre)[7],
                                                       T (&x)[KPT], T *sh) {
@@ -132,11 +134,14 @@ __device__ __forceinline__ void block_affine_scan_pre(const T (&al)[KPT], const 
         if (lane == last) { sh[wid] = A; sh[32 + wid] = pre[5]; }
         __syncthreads();
     }
+    // carry into this warp; the first warp total before it enters as is
     T carry = T(0);
     if (BACK) {
-        for (int v = nw - 1; v > wid; v--) carry = sh[v] + sh[32 + v] * carry;
+        if (wid < nw - 1) carry = sh[nw - 1];
+        for (int v = nw - 2; v > wid; v--) carry = sh[v] + sh[32 + v] * carry;
     } else {
-        for (int v = 0; v < wid; v++) carry = sh[v] + sh[32 + v] * carry;
+        if (wid > 0) carry = sh[0];
+        for (int v = 1; v < wid; v++) carry = sh[v] + sh[32 + v] * carry;
     }
     const T Aprev = BACK ? __shfl_down_sync(FULL, A, 1) : __shfl_up_sync(FULL, A, 1);
     const bool first = BACK ? (lane == 31) : (lane == 0);
@@ -147,7 +152,8 @@ __device__ __forceinline__ void block_affine_scan_pre(const T (&al)[KPT], const 
         xin = al[e] + mu[e] * xin;
         x[e] = xin;
     }
-    if (nw > 1) __syncthreads();
+    // no closing barrier: callers alternate two sh buffers between
+    // consecutive scans, and the next scan's barrier orders the reuse
 }
 
 // ---------------------------------------------------------------------------
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
     if (A.skip && *A.skip) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *const stg = reinterpret_cast<T *>(smem_raw);
-    __shared__ T sh[64];
+    __shared__ T sh[128];   // two buffers: the forward scan uses sh, the backward scan sh + 64
     const bool isY = blockIdx.x == 0;
     const Layout &lay = A.lay;
     const int L = lay.L;
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
             block_affine_scan_pre<T, KPT, false>(al, mu, pf, y, sh);
 #pragma unroll
             for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
-            block_affine_scan_pre<T, KPT, true>(al, mu, pbk, zp, sh);
+            block_affine_scan_pre<T, KPT, true>(al, mu, pbk, zp, sh + 64);
         } else {
             block_affine_scan<T, KPT, false>(al, mu, y, sh);
 #pragma unroll
