@@ -473,21 +473,25 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
                         st_async_rs<DTS_RS>(succ_ring + (unsigned)((P % DTS_NSL) * DTS_RS * sizeof(T)), tz + i * DTS_RS,
                                     succ_rbar + (unsigned)((P % DTS_NSL) * 8));
                 }
-                __syncwarp();   // every lane has read this sub-chunk's ring slots
-                if (has_in && lane == head && !*abort_flag) {
-                    // slots no later sub-chunk reads: re-arm for their next use, release
-                    const int rel = n == nsl - 1 ? nsl : min(n + SKR + 1, nsl);
-                    for (; released < rel; released++) {
-                        const int P = k_in * nsl + released;
-                        mbar_arrive_expect_tx(myrbar + P % DTS_NSL, (unsigned)(DTS_RS * sizeof(T)));
+                // Slots no later sub-chunk reads are re-armed for their next use and
+                // released every fourth sub-chunk and at the strip's end (one warp-wide
+                // branch and two warp barriers per four slots).  The count the
+                // predecessor sees trails the true count by at most three slots, while
+                // the producer needs it only DTS_NSL - 1 slots ahead of the slots this
+                // warp still waits for (n + SKR + 1); a slot is re-armed at least
+                // DTS_NSL - 4 slots before this warp waits on its next phase.
+                if ((n & 3) == 3 || n == nsl - 1) {
+                    __syncwarp();   // every lane has read the ring slots released here
+                    if (has_in && lane == head && !*abort_flag) {
+                        const int rel = n == nsl - 1 ? nsl : min(n + SKR + 1, nsl);
+                        for (; released < rel; released++) {
+                            const int P = k_in * nsl + released;
+                            mbar_arrive_expect_tx(myrbar + P % DTS_NSL, (unsigned)(DTS_RS * sizeof(T)));
+                        }
+                        st_relaxed_cluster(pred_rel, (unsigned)(k_in * nsl + released));
                     }
-                    // the count reaches the predecessor every fourth sub-chunk and at
-                    // the strip's end: it trails the true count by at most three
-                    // slots, while the producer needs it only DTS_NSL - 1 slots
-                    // ahead of the slots this warp still waits for (n + SKR + 1)
-                    if ((n & 3) == 3 || n == nsl - 1) st_relaxed_cluster(pred_rel, (unsigned)(k_in * nsl + released));
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             if (lane == 0) mbar_arrive(myempty + q);   // stage read: the copy warp may refill it
             seq++;
