@@ -178,6 +178,7 @@ struct ChainArgs {
     const T *pre;   // precomputed scan multipliers of this direction (k_line_chain2)
     int nlmax;      // lines per block in the pre layout
     const int *skip;
+    int *err;       // k_line_chain2: BLP_ERR_TIMEOUT if a stage copy never arrives
 };
 
 template <typename T, int KPT>
@@ -263,21 +264,31 @@ __global__ void __launch_bounds__(512) k_line_chain(ChainArgs<T> A) {
 }
 
 // Line chains for L <= 2048 with 16-byte aligned lines (L * sizeof(T) a
-// multiple of 16): the line data (right-hand side, coupling, three factors,
-// boundary term) stream into NS shared-memory stages with 16-byte cp.async,
-// NS-1 lines ahead of the solve.  Thread t owns the KPT consecutive nodes
-// [t*KPT, t*KPT+KPT) of a line; each such segment is followed by 16 bytes
-// of padding, so the 16-byte vector reads of a warp hit distinct banks.
-// NW = 1 keeps both scans inside one warp (no CTA barrier).
+// multiple of 16).  The line data (right-hand side, coupling, three factors
+// and, in FP64, the scan multipliers) arrive in NS shared-memory stages, NS-1
+// lines ahead of the solve.  Thread t owns the KPT consecutive nodes
+// [t*KPT, t*KPT+KPT) of a line.  NW = 1 keeps both scans inside one warp (no
+// CTA barrier).
+// - FP64 (USEPRE): thread 0 issues one bulk copy per array (cp.async.bulk, one
+//   mbarrier per stage, bounded waits) into dense arrays.  Per-thread 16-byte
+//   copies cost the critical warp ~1100 cycles of issue per line (measured);
+//   the dense layout costs 2-way bank conflicts on the 32-byte segments.
+// - FP32: each thread copies 16-byte pieces with cp.async into arrays whose
+//   KPT-element segments are each followed by 16 bytes of padding, so the
+//   vector reads are conflict-free (a dense layout gives 16-element segments
+//   4-way conflicts and measured 43% slower).
+// The boundary term of the last node (two words) comes by cp.async to the
+// thread that owns that node.
 template <typename T, int KPT, int NW, bool USEPRE>
 struct ChainSmem {
     static constexpr int VEC = 16 / sizeof(T);         // elements per 16 bytes
-    static constexpr int LP = 32 * NW * KPT;           // padded line length
-    static constexpr int LPP = LP / KPT * (KPT + VEC);  // with 16 bytes after each segment
+    static constexpr int LP = 32 * NW * KPT;           // line length the threads cover
+    static constexpr int SEG = USEPRE ? KPT : KPT + VEC;   // stride of a thread's segment
+    static constexpr int LPP = LP / KPT * SEG;         // array length in the stage
     static constexpr int PRE = USEPRE ? 14 * 32 * NW : 0;   // scan multipliers: 2 scans x 7 per thread
-    static constexpr size_t stage_elems = (size_t)5 * LPP + VEC + PRE;
+    static constexpr size_t stage_elems = (size_t)5 * LPP + PRE + VEC;   // arrays, multipliers, boundary term
     static constexpr size_t stage = stage_elems * sizeof(T);
-    static __device__ __forceinline__ int at(int e) { return e / KPT * (KPT + VEC) + e % KPT; }
+    static __device__ __forceinline__ int at(int e) { return e / KPT * SEG + e % KPT; }
 };
 
 __device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
@@ -316,31 +327,51 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
     const int e0 = tid * KPT;
     const T *const cpl = TRANS ? (isY ? A.wET : A.wNT) : (isY ? A.wE : A.wN);
     const T *const bcpl = isY ? A.wN : A.wE;
-    const int nvec = L / VEC;
+    const int owner = (L - 1) / KPT;   // the thread that owns the last node
+    __shared__ __align__(8) unsigned long long fullb[NS];
+    __shared__ unsigned abort_flag;
+    if (tid == 0) {
+        for (int q = 0; q < NS; q++) mbar_init(&fullb[q], 1);
+        abort_flag = 0u;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncthreads();
 
-    // line li's data into stage li % NS (one commit group per line)
+    // line li's data into stage li % NS; every thread commits one (possibly
+    // empty) cp.async group per line
     auto issue = [&](int li) {
         if (li < nlines) {
             const int line = TRANS ? li : nlines - 1 - li;
             const long long base = B.off + (long long)line * L;
             T *st = stg + (size_t)(li % NS) * SM::stage_elems;
-            for (int k = tid; k < nvec; k += nthr) {
-                const int e = k * VEC, p = SM::at(e);
-                cp_async_16(st + p, A.v + base + e);
-                cp_async_16(st + SM::LPP + p, cpl + base + e);
-                cp_async_16(st + 2 * SM::LPP + p, A.lf + base + e);
-                cp_async_16(st + 3 * SM::LPP + p, A.lg + base + e);
-                cp_async_16(st + 4 * SM::LPP + p, A.lh + base + e);
+            if constexpr (USEPRE) {
+                if (tid == 0) {
+                    unsigned long long *bar = &fullb[li % NS];
+                    const unsigned lb = (unsigned)(L * sizeof(T));
+                    mbar_arrive_expect_tx(bar, 5u * lb + (unsigned)(SM::PRE * sizeof(T)));
+                    bulk_g2s(st, A.v + base, lb, bar);
+                    bulk_g2s(st + SM::LPP, cpl + base, lb, bar);
+                    bulk_g2s(st + 2 * SM::LPP, A.lf + base, lb, bar);
+                    bulk_g2s(st + 3 * SM::LPP, A.lg + base, lb, bar);
+                    bulk_g2s(st + 4 * SM::LPP, A.lh + base, lb, bar);
+                    // this line's scan multipliers: 14 values per thread, [k][thread]
+                    bulk_g2s(st + 5 * SM::LPP, A.pre + (size_t)(blockIdx.x * A.nlmax + line) * SM::PRE,
+                             (unsigned)(SM::PRE * sizeof(T)), bar);
+                }
+            } else {
+                for (int k = tid; k < L / VEC; k += nthr) {
+                    const int e = k * VEC, p = SM::at(e);
+                    cp_async_16(st + p, A.v + base + e);
+                    cp_async_16(st + SM::LPP + p, cpl + base + e);
+                    cp_async_16(st + 2 * SM::LPP + p, A.lf + base + e);
+                    cp_async_16(st + 3 * SM::LPP + p, A.lg + base + e);
+                    cp_async_16(st + 4 * SM::LPP + p, A.lh + base + e);
+                }
             }
-            if (!TRANS && tid == nthr - 1) {   // boundary term of the last node: coupling * z_I
+            if (!TRANS && tid == owner) {   // boundary term of the last node: coupling * z_I
                 const long long pi = isY ? I.addr(line, 0) : I.addr(0, line);
-                cp_async_word(st + 5 * SM::LPP, bcpl + base + (L - 1));
-                cp_async_word(st + 5 * SM::LPP + 1, A.z + pi);
-            }
-            if (USEPRE) {   // this line's scan multipliers: 14 values per thread, contiguous
-                const T *pre = A.pre + (size_t)(blockIdx.x * A.nlmax + line) * SM::PRE;
-                T *spre = st + 5 * SM::LPP + VEC;
-                for (int k = tid; k < SM::PRE / VEC; k += nthr) cp_async_16(spre + k * VEC, pre + k * VEC);
+                cp_async_word(st + 5 * SM::LPP + SM::PRE, bcpl + base + (L - 1));
+                cp_async_word(st + 5 * SM::LPP + SM::PRE + 1, A.z + pi);
             }
         }
         cp_async_commit();
@@ -354,14 +385,23 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
     }
     for (int li = 0; li < NS - 1; li++) issue(li);
     for (int li = 0; li < nlines; li++) {
-        issue(li + NS - 1);          // the stage of line li-1, read completely by now
-        cp_async_wait<NS - 1>();     // this thread's copies of line li have landed
-        if (NW == 1) __syncwarp(); else __syncthreads();
+        // Stage (li - 1) % NS is refilled here: every thread read it before the
+        // previous line's scans, whose barriers (NW > 1) or shuffles (one warp)
+        // thread 0 has passed.
+        if (USEPRE && NW == 1) __syncwarp();
+        issue(li + NS - 1);
+        if constexpr (USEPRE) {
+            if (!abort_flag) mbar_wait(&fullb[li % NS], (unsigned)(li / NS) & 1u, &abort_flag, A.err);
+            cp_async_wait<NS - 1>();     // the owner's boundary term of line li
+        } else {
+            cp_async_wait<NS - 1>();     // this thread's copies of line li have landed
+            if (NW == 1) __syncwarp(); else __syncthreads();   // and every other thread's
+        }
         const T *st = stg + (size_t)(li % NS) * SM::stage_elems;
         const int line = TRANS ? li : nlines - 1 - li;
         const long long base = B.off + (long long)line * L;
         T vv[KPT], cc[KPT], ff[KPT], g[KPT], hh[KPT];
-        const int p0 = tid * (KPT + VEC);
+        const int p0 = tid * SM::SEG;
 #pragma unroll
         for (int r = 0; r < NV; r++) {
             const int p = p0 + r * VEC;
@@ -372,7 +412,7 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
             *reinterpret_cast<V *>(hh + r * VEC) = *reinterpret_cast<const V *>(st + 4 * SM::LPP + p);
         }
         T bval = T(0);
-        if (!TRANS && e0 <= L - 1 && L - 1 < e0 + KPT) bval = st[5 * SM::LPP] * st[5 * SM::LPP + 1];
+        if (!TRANS && tid == owner) bval = st[5 * SM::LPP + SM::PRE] * st[5 * SM::LPP + SM::PRE + 1];
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
             const int e = e0 + q;
@@ -387,7 +427,7 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
         }
         if constexpr (USEPRE) {
             T pf[7], pbk[7];
-            const T *spre = st + 5 * SM::LPP + VEC;
+            const T *spre = st + 5 * SM::LPP;
 #pragma unroll
             for (int k = 0; k < 7; k++) {
                 pf[k] = spre[k * nthr + tid];
@@ -523,6 +563,7 @@ static int launch_chains(blp_handle *h, const Coefs<T> &c, const T *v, T *z, con
     a.lf = TRANS ? c.lfT : c.lf; a.lg = TRANS ? c.lgT : c.lg; a.lh = TRANS ? c.lhT : c.lh;
     a.pre = nullptr; a.nlmax = 0;
     a.skip = skip;
+    a.err = h->err;
     int L = h->L;
     // per line node: v, coupling, three factors, z = 6 words
     ProfScope ps(h, KC_LINE_CHAIN, (double)(h->lay.R[1].size + h->lay.R[2].size) * sizeof(T) * 6);
