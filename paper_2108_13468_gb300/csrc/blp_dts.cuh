@@ -507,13 +507,13 @@ __global__ void __launch_bounds__(512, 1) k_dts(DtsArgs<T> A, int NST) {
                                             succ_rbar + (unsigned)((P % DTS_NSL) * 8));
                 }
                 // Slots no later sub-chunk reads are re-armed for their next use and
-                // released every fourth sub-chunk and at the strip's end (one warp-wide
-                // branch and two warp barriers per four slots).  The count the
-                // predecessor sees trails the true count by at most three slots, while
+                // released every eighth sub-chunk and at the strip's end (one warp-wide
+                // branch and two warp barriers per eight slots).  The count the
+                // predecessor sees trails the true count by at most seven slots, while
                 // the producer needs it only DTS_NSL - 1 slots ahead of the slots this
                 // warp still waits for (n + SKR + 1); a slot is re-armed at least
-                // DTS_NSL - 4 slots before this warp waits on its next phase.
-                if ((n & 3) == 3 || n == nsl - 1) {
+                // DTS_NSL - 8 slots before this warp waits on its next phase.
+                if ((n & 7) == 7 || n == nsl - 1) {
                     __syncwarp();   // every lane has read the ring slots released here
                     if (has_in && lane == head && !*abort_flag) {
                         const int rel = n == nsl - 1 ? nsl : min(n + SKR + 1, nsl);
