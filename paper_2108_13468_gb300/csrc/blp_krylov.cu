@@ -63,9 +63,10 @@ __global__ void __launch_bounds__(256) k_multidot(const T *__restrict__ V, long 
             const T2 wk = w2[k];
 #pragma unroll
             for (int i = 0; i < NV; i++)
-                if (i < nv) {
+                if (i < nv) {   // two chained FMAs: on GB300 this kernel is FP64-issue-bound
                     const T2 v = reinterpret_cast<const T2 *>(V + i * ld)[k];
-                    acc[i] += v.x * wk.x + v.y * wk.y;
+                    acc[i] = fma(v.x, wk.x, acc[i]);
+                    acc[i] = fma(v.y, wk.y, acc[i]);
                 }
         }
     } else {
@@ -375,6 +376,11 @@ static int setup_ws(blp_handle *h, Workspace &W, bool mixed) {
 // building blocks
 // ---------------------------------------------------------------------------
 static int nblocks(long long np) { return (int)std::min<long long>(BLP_RED_BLOCKS, std::max<long long>(1, (np + 255) / 256)); }
+// Blocks of the Arnoldi dot products: one per SM.  The kernel is bound by
+// GB300's FP64 FMA rate (81% FP64-pipe activity under ncu), and every warp
+// ends with an FP64 shuffle reduction per basis vector, so fewer warps means
+// fewer FP64 instructions for the same products.
+static int nblocks_dot(long long np) { return std::min(nblocks(np), 152); }
 
 
 // out = Op x (mode 0) or f - Op x (mode 1); FP64 operator, x in TX precision
@@ -438,7 +444,7 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
                   int *iters, int *restarts, int *maxcyc, double *res_out, const double *rs, double *vs) {
     const long long np = K.np;
     const int m = K.m;
-    int nb = nblocks(np);
+    int nb = nblocks(np), nbd = nblocks_dot(np);
     int it = 0;
     int rc;
     double res = 0.0;
@@ -484,19 +490,19 @@ static int fgmres(blp_handle *h, KWork<TZ> &K, const double *b, double *x, int t
             int nv = j + 1;
             double *h1 = K.hbuf, *h2 = K.hbuf + MAXV, *nr = K.hbuf + 2 * MAXV;
             { ProfScope ps_(h, KC_MULTIDOT, (double)np * sizeof(double) * (nv + 1));
-              launch_multidot<double>(h, nb, K.V, np, nv, K.w, np, h->partials);
+              launch_multidot<double>(h, nbd, K.V, np, nv, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
-              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h1, nullptr, nullptr);
+              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nbd, nv, h1, nullptr, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
               launch_update<double>(h, nb, K.V, np, nv, h1, K.w, np, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_MULTIDOT, (double)np * sizeof(double) * (nv + 1));
-              launch_multidot<double>(h, nb, K.V, np, nv, K.w, np, h->partials);
+              launch_multidot<double>(h, nbd, K.V, np, nv, K.w, np, h->partials);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_SMALL);
-              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nb, nv, h2, nullptr, nullptr);
+              k_reduce<<<1, reduce_threads(nv), 0, h->stream>>>(h->partials, nbd, nv, h2, nullptr, nullptr);
               LAUNCH_CHECK(h); }
             { ProfScope ps_(h, KC_UPDATE, (double)np * sizeof(double) * (nv + 2));
               launch_update<double>(h, nb, K.V, np, nv, h2, K.w, np, h->partials);
@@ -631,7 +637,7 @@ static TZ *precond_input(Workspace &W, KWork<TZ> &K) {
 template <typename TZ>
 static int capture_iteration(blp_handle *h, Workspace &W, KWork<TZ> &K, int trans, cudaGraphConditionalHandle hI) {
     const long long np = K.np;
-    const int m = K.m, nb = nblocks(np);
+    const int m = K.m, nb = nblocks(np), nbd = nblocks_dot(np);
     const int *jdev = &W.ctl->j;
     TZ *vin = precond_input<TZ>(W, K);   // V_j, written when V_j was formed
     TZ *zg = static_cast<TZ *>(W.zg);
@@ -639,15 +645,15 @@ static int capture_iteration(blp_handle *h, Workspace &W, KWork<TZ> &K, int tran
     int rc, cyc = 0;
     if ((rc = precond_apply<TZ>(h, vin, zg, trans, &cyc))) return rc;
     if ((rc = matvec<TZ>(h, zg, K.w, nullptr, 0, trans, nullptr, K.Z, jdev))) return rc;   // and Z_j = z
-    launch_multidot<double>(h, nb, K.V, np, m, K.w, np, h->partials, jdev);
+    launch_multidot<double>(h, nbd, K.V, np, m, K.w, np, h->partials, jdev);
     LAUNCH_CHECK(h);
-    k_reduce<<<1, reduce_threads(m), 0, h->stream>>>(h->partials, nb, m, h1, nullptr, jdev);
+    k_reduce<<<1, reduce_threads(m), 0, h->stream>>>(h->partials, nbd, m, h1, nullptr, jdev);
     LAUNCH_CHECK(h);
     launch_update<double>(h, nb, K.V, np, m, h1, K.w, np, nullptr, jdev);
     LAUNCH_CHECK(h);
-    launch_multidot<double>(h, nb, K.V, np, m, K.w, np, h->partials, jdev);
+    launch_multidot<double>(h, nbd, K.V, np, m, K.w, np, h->partials, jdev);
     LAUNCH_CHECK(h);
-    k_reduce<<<1, reduce_threads(m), 0, h->stream>>>(h->partials, nb, m, h2, nullptr, jdev);
+    k_reduce<<<1, reduce_threads(m), 0, h->stream>>>(h->partials, nbd, m, h2, nullptr, jdev);
     LAUNCH_CHECK(h);
     launch_update<double>(h, nb, K.V, np, m, h2, K.w, np, h->partials, jdev);
     LAUNCH_CHECK(h);
