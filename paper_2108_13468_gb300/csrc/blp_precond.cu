@@ -42,9 +42,13 @@ __global__ void k_gs_rhs(Region R, const T *__restrict__ b, const T *__restrict_
 // Warp-level Kogge-Stone over the per-thread compositions, then the warp
 // totals are composed serially (few warps) through shared memory.
 // ---------------------------------------------------------------------------
+// nw: the warps taking part (all of the block's by default); with one warp
+// the scan uses no block barrier, so other warps of the block may run other code.
 template <typename T, int KPT, bool BACK>
-__device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&mu)[KPT], T (&x)[KPT], T *sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&mu)[KPT], T (&x)[KPT], T *sh,
+                                                  int nw = -1) {
+    if (nw < 0) nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T A = T(0), M = T(1);
 #pragma unroll
     for (int q = 0; q < KPT; q++) {
@@ -60,8 +64,10 @@ __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&
         if (ok) { A = A + M * Ap; M = M * Mp; }
     }
     const int last = BACK ? 0 : 31;
-    if (lane == last) { sh[wid] = A; sh[32 + wid] = M; }
-    __syncthreads();
+    if (nw > 1) {
+        if (lane == last) { sh[wid] = A; sh[32 + wid] = M; }
+        __syncthreads();
+    }
     // carry into this warp: composition of the warps before it in sequence order
     T carry = T(0);
     if (BACK) {
@@ -79,7 +85,7 @@ __device__ __forceinline__ void block_affine_scan(const T (&al)[KPT], const T (&
         xin = al[e] + mu[e] * xin;
         x[e] = xin;
     }
-    __syncthreads();
+    if (nw > 1) __syncthreads();
 }
 
 // The multipliers of block_affine_scan do not depend on the right-hand side:
@@ -308,9 +314,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// FP32 with one compute warp: a second warp issues the cp.async copies of the
+// next lines (a line's copies complete the stage's full mbarrier through
+// cp.async.mbarrier.arrive.noinc; the compute warp frees the stage with an
+// arrive on its empty mbarrier), so the compute warp issues no copies.  A
+// clock64 trace had that issue at ~570 of ~1980 cycles per line.
+template <typename T, int NW, bool USEPRE> struct ChainCopyWarp { static constexpr bool on = !USEPRE && NW == 1; };
+
 template <typename T, int KPT, int NW, int NS, bool TRANS, bool USEPRE>
-__global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
+__global__ void __launch_bounds__(32 * NW + 32) k_line_chain2(ChainArgs<T> A) {
     typedef ChainSmem<T, KPT, NW, USEPRE> SM;
+    constexpr bool CW = ChainCopyWarp<T, NW, USEPRE>::on;
     constexpr int VEC = SM::VEC, NV = KPT / VEC;
     typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
     if (A.skip && *A.skip) return;
@@ -328,14 +342,49 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
     const T *const cpl = TRANS ? (isY ? A.wET : A.wNT) : (isY ? A.wE : A.wN);
     const T *const bcpl = isY ? A.wN : A.wE;
     const int owner = (L - 1) / KPT;   // the thread that owns the last node
-    __shared__ __align__(8) unsigned long long fullb[NS];
+    __shared__ __align__(8) unsigned long long fullb[NS], emptyb[NS];
     __shared__ unsigned abort_flag;
     if (tid == 0) {
-        for (int q = 0; q < NS; q++) mbar_init(&fullb[q], 1);
+        for (int q = 0; q < NS; q++) {
+            mbar_init(&fullb[q], CW ? 32 : 1);   // copy warp: one arrival per lane and line
+            mbar_init(&emptyb[q], 1);
+        }
         abort_flag = 0u;
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     __syncthreads();
+
+    if constexpr (CW) {
+        if (tid >= 32 * NW) {   // ---- copy warp ----
+            const int lane = tid & 31;
+            for (int li = 0; li < nlines; li++) {
+                const int q = li % NS, u = li / NS;
+                if (u > 0) {   // the compute warp has read the line that used this stage before
+                    mbar_wait(&emptyb[q], (unsigned)(u - 1) & 1u, &abort_flag, A.err);
+                    if (abort_flag) break;
+                }
+                const int line = TRANS ? li : nlines - 1 - li;
+                const long long base = B.off + (long long)line * L;
+                T *st = stg + (size_t)q * SM::stage_elems;
+                for (int k = lane; k < L / VEC; k += 32) {
+                    const int e = k * VEC, p = SM::at(e);
+                    cp_async_16(st + p, A.v + base + e);
+                    cp_async_16(st + SM::LPP + p, cpl + base + e);
+                    cp_async_16(st + 2 * SM::LPP + p, A.lf + base + e);
+                    cp_async_16(st + 3 * SM::LPP + p, A.lg + base + e);
+                    cp_async_16(st + 4 * SM::LPP + p, A.lh + base + e);
+                }
+                if (!TRANS && lane == 31) {   // boundary term of the last node: coupling * z_I
+                    const long long pi = isY ? I.addr(line, 0) : I.addr(0, line);
+                    cp_async_word(st + 5 * SM::LPP + SM::PRE, bcpl + base + (L - 1));
+                    cp_async_word(st + 5 * SM::LPP + SM::PRE + 1, A.z + pi);
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&fullb[q])) : "memory");
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy lands after the CTA exits
+            return;
+        }
+    }
 
     // line li's data into stage li % NS; every thread commits one (possibly
     // empty) cp.async group per line
@@ -383,14 +432,17 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
         const int e = e0 + q;
         zp[q] = (TRANS && e < L && nlines > 0) ? A.z[isY ? C.addr(L - 1, e) : C.addr(e, L - 1)] : T(0);
     }
-    for (int li = 0; li < NS - 1; li++) issue(li);
+    if (!CW)
+        for (int li = 0; li < NS - 1; li++) issue(li);
     for (int li = 0; li < nlines; li++) {
         // Stage (li - 1) % NS is refilled here: every thread read it before the
         // previous line's scans, whose barriers (NW > 1) or shuffles (one warp)
         // thread 0 has passed.
         if (USEPRE && NW == 1) __syncwarp();
-        issue(li + NS - 1);
-        if constexpr (USEPRE) {
+        if (!CW) issue(li + NS - 1);
+        if constexpr (CW) {
+            if (!abort_flag) mbar_wait(&fullb[li % NS], (unsigned)(li / NS) & 1u, &abort_flag, A.err);
+        } else if constexpr (USEPRE) {
             if (!abort_flag) mbar_wait(&fullb[li % NS], (unsigned)(li / NS) & 1u, &abort_flag, A.err);
             cp_async_wait<NS - 1>();     // the owner's boundary term of line li
         } else {
@@ -413,6 +465,10 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
         }
         T bval = T(0);
         if (!TRANS && tid == owner) bval = st[5 * SM::LPP + SM::PRE] * st[5 * SM::LPP + SM::PRE + 1];
+        if constexpr (CW) {   // stage read: the copy warp may refill it
+            __syncwarp();
+            if (tid == 0) mbar_arrive(&emptyb[li % NS]);
+        }
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
             const int e = e0 + q;
@@ -438,10 +494,10 @@ __global__ void __launch_bounds__(32 * NW) k_line_chain2(ChainArgs<T> A) {
             for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
             block_affine_scan_pre<T, KPT, true>(al, mu, pbk, zp, sh + 64);
         } else {
-            block_affine_scan<T, KPT, false>(al, mu, y, sh);
+            block_affine_scan<T, KPT, false>(al, mu, y, sh, NW);
 #pragma unroll
             for (int q = 0; q < KPT; q++) { al[q] = g[q] * y[q]; mu[q] = hh[q]; }
-            block_affine_scan<T, KPT, true>(al, mu, zp, sh);
+            block_affine_scan<T, KPT, true>(al, mu, zp, sh, NW);
         }
 #pragma unroll
         for (int r = 0; r < NV; r++)
@@ -550,7 +606,8 @@ static int launch_chain2(blp_handle *h, const ChainArgs<T> &a) {
     constexpr size_t smem = NS * ChainSmem<T, KPT, NW, USEPRE>::stage;
     static_assert(smem <= 225 * 1024, "line-chain stages exceed the shared-memory budget");
     if (!chain2_attrs_once<T, KPT, NW, NS, TRANS>()) return BLP_ERR_CUDA;
-    k_line_chain2<T, KPT, NW, NS, TRANS, USEPRE><<<2, 32 * NW, smem, h->stream>>>(a);
+    k_line_chain2<T, KPT, NW, NS, TRANS, USEPRE>
+        <<<2, 32 * NW + (ChainCopyWarp<T, NW, USEPRE>::on ? 32 : 0), smem, h->stream>>>(a);
     LAUNCH_CHECK(h);
     return BLP_OK;
 }
