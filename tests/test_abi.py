@@ -118,3 +118,35 @@ def test_host_side_argument_checks_of_the_newer_entry_points():
     assert lib.blp_solve_1d_batched(probs, 3, None) == _native.BLP_ERR_ARG
     assert [probs[k].status for k in range(3)] == [_native.BLP_ERR_ARG] * 3
     assert all(probs[k].iters == 0 and probs[k].resid == -1.0 for k in range(3))
+
+
+STRUCTS = [("blp_params", _native.Params), ("blp_info", _native.Info), ("blp_batch_item", _native.BatchItem),
+           ("blp_tuning", _native.Tuning), ("blp_1d_problem", _native.Problem1D)]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs agree with the C compiler's layout
+    of include/blp.h: size and every field's offset."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "blp.h"', "int main(void) {"]
+    for cname, py in STRUCTS:
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        struct, field, value = line.split()
+        got[(struct, field)] = int(value)
+    for cname, py in STRUCTS:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
